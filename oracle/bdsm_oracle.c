@@ -1,0 +1,327 @@
+/*
+ * bdsm_oracle.c -- plain, slow, single-threaded CPU oracle for batch-dynamic
+ * subgraph matching (BDSM).  TEST INFRASTRUCTURE ONLY: it exists to check the
+ * CUDA path and is never part of it.  It shares no code with the library.
+ *
+ * What it computes (Sec. II-A, Def. 1 and Def. 2, Problem Statement):
+ *   G' = (E(G) \ D) u I for a batch with insertions I and deletions D.
+ *   An embedding (Def. 2) is an injective map phi: V(Q) -> V(G) with
+ *   L(phi(u)) = L(u) for every query vertex and (phi(u), phi(u')) an edge for
+ *   every query edge (non-induced).  The incremental matches are
+ *     positive: Emb(Q, G') \ Emb(Q, G)   (embeddings using >= 1 inserted edge)
+ *     negative: Emb(Q, G)  \ Emb(Q, G')  (embeddings using >= 1 deleted edge)
+ *   and each one is charged to the lowest-indexed update of its own sign among
+ *   the update edges that are images of query edges (Sec. IV-C, the total
+ *   order over updates used to remove duplicates).
+ *
+ * How: for each update i (sign s, view V = G' if s = + else G), for each
+ * query edge (a, b) and each of the two orientations of the undirected update
+ * edge, fix phi(a), phi(b) to its endpoints when the labels agree, then
+ * backtrack over the other query vertices in a fixed order in which every
+ * vertex has an already-assigned query neighbour (the query is connected),
+ * trying every V-neighbour of the image of one assigned query neighbour (the
+ * one whose image has the fewest view neighbours).  A candidate
+ * is kept when its label matches, it is not already used, and for EVERY query
+ * edge to an assigned vertex the image edge is in V and is not an update of
+ * sign s with index < i.  No filter, no encoding, no reordering: membership is
+ * a hash-set lookup.
+ *
+ * Batch validity (a reading: the paper is silent): a batch is rejected as a
+ * whole when any update has an out-of-range id, a self-loop, an op other than
+ * +1/-1, repeats an edge already in the batch, inserts an edge present in G
+ * or deletes one absent from G.  The reported offender is the smallest index
+ * k such that update k is invalid on its own or repeats an earlier update.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_EINVAL (-1)
+#define OR_EBUDGET (-2)
+#define OR_ENOMEM (-3)
+
+/* ---------------- open-addressing hash map: edge key -> int64 value ------ */
+typedef struct {
+  uint64_t *keys; /* 0 = empty; stored key = real key + 1 */
+  int64_t *vals;
+  uint64_t mask;
+} hmap;
+
+static uint64_t hmix(uint64_t z) {
+  z ^= z >> 33; z *= 0xff51afd7ed558ccdULL;
+  z ^= z >> 33; z *= 0xc4ceb9fe1a85ec53ULL;
+  z ^= z >> 33; return z;
+}
+
+static int hmap_init(hmap *h, int64_t n) {
+  uint64_t cap = 16;
+  while (cap < (uint64_t)(2 * n + 16)) cap <<= 1;
+  h->keys = (uint64_t *)calloc(cap, sizeof(uint64_t));
+  h->vals = (int64_t *)malloc(cap * sizeof(int64_t));
+  h->mask = cap - 1;
+  return (h->keys && h->vals) ? 0 : -1;
+}
+
+static void hmap_free(hmap *h) { free(h->keys); free(h->vals); }
+
+/* returns 1 if inserted, 0 if present (value untouched) */
+static int hmap_put(hmap *h, uint64_t key, int64_t val) {
+  uint64_t k = key + 1, i = hmix(k) & h->mask;
+  while (h->keys[i]) {
+    if (h->keys[i] == k) return 0;
+    i = (i + 1) & h->mask;
+  }
+  h->keys[i] = k; h->vals[i] = val; return 1;
+}
+
+static int hmap_get(const hmap *h, uint64_t key, int64_t *val) {
+  uint64_t k = key + 1, i = hmix(k) & h->mask;
+  while (h->keys[i]) {
+    if (h->keys[i] == k) { if (val) *val = h->vals[i]; return 1; }
+    i = (i + 1) & h->mask;
+  }
+  return 0;
+}
+
+static uint64_t ekey(int32_t a, int32_t b) {
+  uint32_t lo = (uint32_t)(a < b ? a : b), hi = (uint32_t)(a < b ? b : a);
+  return ((uint64_t)lo << 32) | hi;
+}
+
+/* ---------------- adjacency lists (for iteration only) -------------------- */
+typedef struct { int64_t *off; int32_t *nbr; } adj;
+
+static int adj_build(adj *A, int32_t n, int64_t m, const int32_t *s, const int32_t *d) {
+  A->off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  A->nbr = (int32_t *)malloc((size_t)(2 * m + 1) * sizeof(int32_t));
+  if (!A->off || !A->nbr) return -1;
+  for (int64_t e = 0; e < m; e++) { A->off[s[e] + 1]++; A->off[d[e] + 1]++; }
+  for (int32_t v = 0; v < n; v++) A->off[v + 1] += A->off[v];
+  int64_t *fill = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+  if (!fill) return -1;
+  memcpy(fill, A->off, ((size_t)n + 1) * sizeof(int64_t));
+  for (int64_t e = 0; e < m; e++) {
+    A->nbr[fill[s[e]]++] = d[e];
+    A->nbr[fill[d[e]]++] = s[e];
+  }
+  free(fill);
+  return 0;
+}
+
+static void adj_free(adj *A) { free(A->off); free(A->nbr); }
+
+/* ---------------- search state --------------------------------------------- */
+typedef struct {
+  int32_t q;
+  const int32_t *qlab;
+  int32_t eq;
+  const int32_t *qs, *qd;
+  const int32_t *lab;
+  const hmap *gset;   /* edges of G */
+  const hmap *bmap;   /* batch edge -> update index */
+  const int8_t *op;
+  const adj *view;
+  int sign;           /* +1 / -1 of the seeding update */
+  int64_t upd;        /* index of the seeding update */
+  int32_t order[32];  /* search order after the two seeded vertices */
+  int32_t anchor[32]; /* an assigned query neighbour of order[t] */
+  int32_t phi[32];
+  uint8_t used_q[32];
+  uint64_t count;
+  uint64_t nodes, budget;
+  int32_t *tuples; int64_t tuple_cap; int64_t *n_tuples;
+  int over_budget;
+} srch;
+
+/* Is data edge (x, y) an edge of the seed's view, and not an update of the
+ * seed's sign with a smaller index (charging rule)? */
+static int edge_ok(const srch *S, int32_t x, int32_t y) {
+  uint64_t k = ekey(x, y);
+  int64_t bi;
+  if (hmap_get(S->bmap, k, &bi)) {
+    int bs = S->op[bi];
+    if (bs != S->sign) return 0;      /* +: deleted edge not in G'; -: inserted edge not in G */
+    return bi >= S->upd;              /* same sign: only later-or-equal updates */
+  }
+  return hmap_get(S->gset, k, NULL);  /* untouched edge: in G iff in G' */
+}
+
+/* every query edge between u and an assigned query vertex maps into the view */
+static int all_edges_ok(const srch *S, int32_t u, int32_t c) {
+  for (int32_t e = 0; e < S->eq; e++) {
+    int32_t a = S->qs[e], b = S->qd[e], w;
+    if (a == u) w = b; else if (b == u) w = a; else continue;
+    if (!S->used_q[w]) continue;
+    if (!edge_ok(S, c, S->phi[w])) return 0;
+  }
+  return 1;
+}
+
+static void emit(srch *S) {
+  S->count++;
+  if (S->tuples && S->n_tuples) {
+    int64_t t = *S->n_tuples;
+    if (t < S->tuple_cap) {
+      int32_t *r = S->tuples + t * (2 + S->q);
+      r[0] = (int32_t)S->upd; r[1] = S->sign;
+      for (int32_t u = 0; u < S->q; u++) r[2 + u] = S->phi[u];
+    }
+    *S->n_tuples = t + 1;
+  }
+}
+
+static void extend(srch *S, int32_t t) {
+  if (S->over_budget) return;
+  if (t == S->q) { emit(S); return; }
+  int32_t u = S->order[t];
+  const adj *A = S->view;
+  /* every valid image of u is a view-neighbour of the image of each assigned
+   * query neighbour of u; scan the shortest of those neighbour lists */
+  int32_t x = S->phi[S->anchor[t]];
+  for (int32_t e = 0; e < S->eq; e++) {
+    int32_t a = S->qs[e], b = S->qd[e], w;
+    if (a == u) w = b; else if (b == u) w = a; else continue;
+    if (!S->used_q[w]) continue;
+    int32_t y = S->phi[w];
+    if (A->off[y + 1] - A->off[y] < A->off[x + 1] - A->off[x]) x = y;
+  }
+  for (int64_t p = A->off[x]; p < A->off[x + 1]; p++) {
+    int32_t c = A->nbr[p];
+    if (++S->nodes > S->budget && S->budget) { S->over_budget = 1; return; }
+    if (S->lab[c] != S->qlab[u]) continue;
+    int dup = 0;
+    for (int32_t w = 0; w < S->q; w++)
+      if (S->used_q[w] && S->phi[w] == c) { dup = 1; break; }
+    if (dup) continue;
+    if (!all_edges_ok(S, u, c)) continue;
+    S->phi[u] = c; S->used_q[u] = 1;
+    extend(S, t + 1);
+    S->used_q[u] = 0;
+  }
+}
+
+/* order for a seeded query edge (a, b): repeatedly take the smallest-id
+ * unassigned vertex that has an assigned neighbour; anchor = that neighbour
+ * with the smallest id.  Returns 0 if Q is disconnected. */
+static int make_order(srch *S, int32_t a, int32_t b) {
+  uint8_t in[32] = {0};
+  in[a] = in[b] = 1;
+  S->order[0] = a; S->order[1] = b;
+  for (int32_t t = 2; t < S->q; t++) {
+    int32_t pick = -1, anc = -1;
+    for (int32_t u = 0; u < S->q && pick < 0; u++) {
+      if (in[u]) continue;
+      for (int32_t w = 0; w < S->q; w++) {
+        if (!in[w]) continue;
+        int adjq = 0;
+        for (int32_t e = 0; e < S->eq; e++)
+          if ((S->qs[e] == u && S->qd[e] == w) || (S->qs[e] == w && S->qd[e] == u)) { adjq = 1; break; }
+        if (adjq) { pick = u; anc = w; break; }
+      }
+    }
+    if (pick < 0) return 0;
+    in[pick] = 1; S->order[t] = pick; S->anchor[t] = anc;
+  }
+  return 1;
+}
+
+/*
+ * oracle_bdsm: incremental matches of one query for one batch.
+ *   graph G: n vertices with labels[n]; m undirected edges (src[e], dst[e])
+ *            (duplicates merged; self-loops or bad ids -> OR_EINVAL, bad_index = -1)
+ *   query Q: q <= 31 vertices, qlabels[q], eq edges (qsrc, qdst); must be connected
+ *   batch:   b updates (op[k] = +1/-1, usrc[k], udst[k])
+ *   eval:    n_eval update indices to evaluate (eval_idx == NULL: all b, in order)
+ *   out_count[j]: number of incremental matches charged to update eval_idx[j]
+ *   tuples:  if non-NULL, rows of (update, sign, phi[0..q-1]) up to tuple_cap rows;
+ *            *n_tuples receives the number of rows produced (may exceed the cap)
+ *   node_budget: 0 = unlimited, else OR_EBUDGET once that many candidates were tried
+ * Returns OR_OK, OR_EINVAL (bad_index = offending update), OR_EBUDGET, OR_ENOMEM.
+ */
+int oracle_bdsm(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
+                int32_t q, const int32_t *qlabels, int32_t eq, const int32_t *qsrc, const int32_t *qdst,
+                int64_t b, const int8_t *op, const int32_t *usrc, const int32_t *udst,
+                int64_t n_eval, const int64_t *eval_idx, uint64_t *out_count,
+                int32_t *tuples, int64_t tuple_cap, int64_t *n_tuples,
+                uint64_t node_budget, int64_t *bad_index) {
+  if (bad_index) *bad_index = -1;
+  if (n_tuples) *n_tuples = 0;
+  if (q < 2 || q > 31 || eq < 1) return OR_EINVAL;
+  for (int32_t e = 0; e < eq; e++)
+    if (qsrc[e] < 0 || qsrc[e] >= q || qdst[e] < 0 || qdst[e] >= q || qsrc[e] == qdst[e]) return OR_EINVAL;
+
+  hmap gset, bmap;
+  if (hmap_init(&gset, m) || hmap_init(&bmap, b)) return OR_ENOMEM;
+  int32_t *gs = (int32_t *)malloc((size_t)(m + 1) * sizeof(int32_t));
+  int32_t *gd = (int32_t *)malloc((size_t)(m + 1) * sizeof(int32_t));
+  int64_t mu = 0;
+  for (int64_t e = 0; e < m; e++) {
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n || src[e] == dst[e]) {
+      hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd); return OR_EINVAL;
+    }
+    if (hmap_put(&gset, ekey(src[e], dst[e]), 0)) { gs[mu] = src[e]; gd[mu] = dst[e]; mu++; }
+  }
+  /* batch validation, in index order */
+  for (int64_t k = 0; k < b; k++) {
+    int32_t x = usrc[k], y = udst[k];
+    int bad = (op[k] != 1 && op[k] != -1) || x < 0 || x >= n || y < 0 || y >= n || x == y;
+    if (!bad) {
+      uint64_t kk = ekey(x, y);
+      int ing = hmap_get(&gset, kk, NULL);
+      if (!hmap_put(&bmap, kk, k)) bad = 1;
+      else if (op[k] == 1 && ing) bad = 1;
+      else if (op[k] == -1 && !ing) bad = 1;
+    }
+    if (bad) {
+      if (bad_index) *bad_index = k;
+      hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd); return OR_EINVAL;
+    }
+  }
+  /* G' edge list */
+  int32_t *ps = (int32_t *)malloc((size_t)(mu + b + 1) * sizeof(int32_t));
+  int32_t *pd = (int32_t *)malloc((size_t)(mu + b + 1) * sizeof(int32_t));
+  int64_t mp = 0;
+  for (int64_t e = 0; e < mu; e++) {
+    int64_t bi;
+    if (hmap_get(&bmap, ekey(gs[e], gd[e]), &bi) && op[bi] == -1) continue;
+    ps[mp] = gs[e]; pd[mp] = gd[e]; mp++;
+  }
+  for (int64_t k = 0; k < b; k++)
+    if (op[k] == 1) { ps[mp] = usrc[k]; pd[mp] = udst[k]; mp++; }
+  adj AG, AP;
+  if (adj_build(&AG, n, mu, gs, gd) || adj_build(&AP, n, mp, ps, pd)) return OR_ENOMEM;
+  free(ps); free(pd);
+
+  srch S;
+  memset(&S, 0, sizeof(S));
+  S.q = q; S.qlab = qlabels; S.eq = eq; S.qs = qsrc; S.qd = qdst; S.lab = labels;
+  S.gset = &gset; S.bmap = &bmap; S.op = op; S.budget = node_budget;
+  S.tuples = tuples; S.tuple_cap = tuple_cap; S.n_tuples = n_tuples;
+
+  int rc = OR_OK;
+  int64_t ne = eval_idx ? n_eval : b;
+  for (int64_t j = 0; j < ne && rc == OR_OK; j++) {
+    int64_t i = eval_idx ? eval_idx[j] : j;
+    if (i < 0 || i >= b) { rc = OR_EINVAL; break; }
+    S.sign = op[i]; S.upd = i; S.view = (op[i] == 1) ? &AP : &AG;
+    S.count = 0;
+    for (int32_t e = 0; e < eq; e++) {
+      for (int o = 0; o < 2; o++) {
+        int32_t a = qsrc[e], bq = qdst[e];
+        int32_t x = o ? udst[i] : usrc[i], y = o ? usrc[i] : udst[i];
+        if (labels[x] != qlabels[a] || labels[y] != qlabels[bq]) continue;
+        if (!make_order(&S, a, bq)) { rc = OR_EINVAL; break; }
+        memset(S.used_q, 0, sizeof(S.used_q));
+        S.phi[a] = x; S.phi[bq] = y; S.used_q[a] = S.used_q[bq] = 1;
+        extend(&S, 2);
+        if (S.over_budget) { rc = OR_EBUDGET; break; }
+      }
+      if (rc != OR_OK) break;
+    }
+    if (out_count) out_count[j] = S.count;
+  }
+  adj_free(&AG); adj_free(&AP);
+  hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd);
+  return rc;
+}

@@ -1,0 +1,211 @@
+"""CPU oracle for batch-dynamic subgraph matching -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg use this
+module; the library never does. It shares no code with the CUDA path: the
+only import from the package is the seeded input generator module, which
+holds no matching arithmetic.
+
+Two independent programs compute the same thing, the plain definition of the
+incremental matches of a batch (Sec. II-A, Def. 1, Def. 2, Problem Statement):
+
+* ``bdsm`` (O2) calls ``bdsm_oracle.c``: per update, per query edge, per
+  orientation, a backtracking search in the view of the update's sign
+  (G' for insertions, G for deletions) that refuses image edges which are
+  same-sign updates of smaller index, so each match is charged once, to its
+  lowest-indexed update (Sec. IV-C, total order over updates).
+* ``brute_bdsm`` (O1, pure Python, tiny inputs): enumerate Emb(Q, G) and
+  Emb(Q, G') by trying every data vertex for every query vertex, take the two
+  set differences, and charge each match to its lowest-indexed update.
+
+Readings of points the paper leaves open are those listed in the oracle's C
+header (batch validity) and: matches are embeddings (automorphic images are
+distinct results); edges are undirected, so an update is tried in both
+orientations on every query edge.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+from typing import Dict, Iterable, List, Optional, Sequence, Set, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "bdsm_oracle.c")
+
+OK, EINVAL, EBUDGET, ENOMEM = 0, -1, -2, -3
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (portable flags, no -march)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        p = ctypes.c_void_p
+        lib.oracle_bdsm.restype = ctypes.c_int
+        lib.oracle_bdsm.argtypes = [
+            ctypes.c_int32, p, ctypes.c_int64, p, p,
+            ctypes.c_int32, p, ctypes.c_int32, p, p,
+            ctypes.c_int64, p, p, p,
+            ctypes.c_int64, p, p,
+            p, ctypes.c_int64, p,
+            ctypes.c_uint64, p]
+        _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, bad_index: int):
+        super().__init__("oracle error %d (bad update index %d)" % (code, bad_index))
+        self.code = code
+        self.bad_index = bad_index
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def bdsm(n: int, labels, src, dst, query, batch, eval_idx: Optional[Sequence[int]] = None,
+         want_tuples: bool = False, tuple_cap: int = 1 << 22, budget: int = 0):
+    """O2: incremental matches of ``query`` for ``batch`` on graph (n, labels, src, dst).
+
+    Returns (counts, tuples): counts[j] = matches charged to update eval_idx[j]
+    (all updates when eval_idx is None); tuples is an int32 array of rows
+    (update, sign, phi[0..q-1]) or None. Raises OracleError on invalid input
+    or when ``budget`` (candidate tests) is exceeded.
+    """
+    lib = _load()
+    labels = np.ascontiguousarray(labels, np.int32)
+    src = np.ascontiguousarray(src, np.int32)
+    dst = np.ascontiguousarray(dst, np.int32)
+    ql = np.ascontiguousarray(query.labels, np.int32)
+    qs = np.ascontiguousarray(query.src, np.int32)
+    qd = np.ascontiguousarray(query.dst, np.int32)
+    op = np.ascontiguousarray(batch.op, np.int8)
+    us = np.ascontiguousarray(batch.src, np.int32)
+    ud = np.ascontiguousarray(batch.dst, np.int32)
+    b = op.size
+    ev = None if eval_idx is None else np.ascontiguousarray(eval_idx, np.int64)
+    ne = b if ev is None else ev.size
+    counts = np.zeros(max(ne, 1), np.uint64)
+    tup = np.zeros((tuple_cap, 2 + ql.size), np.int32) if want_tuples else None
+    nt = ctypes.c_int64(0)
+    bad = ctypes.c_int64(-1)
+    rc = lib.oracle_bdsm(n, _ptr(labels), src.size, _ptr(src), _ptr(dst),
+                         ql.size, _ptr(ql), qs.size, _ptr(qs), _ptr(qd),
+                         b, _ptr(op), _ptr(us), _ptr(ud),
+                         ne, _ptr(ev), _ptr(counts),
+                         _ptr(tup), tuple_cap if want_tuples else 0,
+                         ctypes.byref(nt) if want_tuples else None,
+                         budget, ctypes.byref(bad))
+    if rc != OK:
+        raise OracleError(rc, bad.value)
+    counts = counts[:ne]
+    if want_tuples:
+        if nt.value > tuple_cap:
+            raise OracleError(ENOMEM, -1)
+        tup = tup[:nt.value]
+    return counts, tup
+
+
+def totals(counts: np.ndarray, op: np.ndarray, eval_idx=None) -> Tuple[int, int]:
+    """(positive, negative) totals from per-update charged counts."""
+    sg = np.asarray(op)[np.arange(len(op)) if eval_idx is None else np.asarray(eval_idx)]
+    c = counts.astype(np.uint64)
+    return int(c[sg > 0].sum()), int(c[sg < 0].sum())
+
+
+def canonical_tuples(tuples: np.ndarray) -> np.ndarray:
+    """Rows (sign, phi...) sorted lexicographically, '+' before '-'; the update
+    column is dropped (compared separately as per-update counts)."""
+    if tuples is None or tuples.size == 0:
+        return np.zeros((0, 0 if tuples is None else tuples.shape[1] - 1), np.int64)
+    rows = tuples[:, 1:].astype(np.int64).copy()
+    rows[:, 0] = np.where(rows[:, 0] > 0, 0, 1)
+    order = np.lexsort(rows.T[::-1])
+    return rows[order]
+
+
+# ---------------------------------------------------------------------------
+# O1: brute-force static difference (pure Python, tiny graphs only)
+# ---------------------------------------------------------------------------
+
+def _edge(a: int, b: int) -> Tuple[int, int]:
+    return (a, b) if a < b else (b, a)
+
+
+def brute_embeddings(n: int, labels, edges: Set[Tuple[int, int]], query) -> Set[Tuple[int, ...]]:
+    """Every injective label-preserving map V(Q) -> V(G) whose query edges are
+    all data edges (Def. 2), by trying every data vertex for every query
+    vertex in id order and checking edges as soon as both ends are placed."""
+    q = query.q
+    ql = [int(x) for x in query.labels]
+    qe = [(int(a), int(b)) for a, b in zip(query.src, query.dst)]
+    lab = [int(x) for x in labels]
+    nbrs_before = [[] for _ in range(q)]  # query edges (u, w) with w < u
+    for a, b in qe:
+        hi, lo = max(a, b), min(a, b)
+        nbrs_before[hi].append(lo)
+    out: Set[Tuple[int, ...]] = set()
+    phi = [-1] * q
+
+    def rec(u: int):
+        if u == q:
+            out.add(tuple(phi))
+            return
+        for v in range(n):
+            if lab[v] != ql[u] or v in phi[:u]:
+                continue
+            if all(_edge(v, phi[w]) in edges for w in nbrs_before[u]):
+                phi[u] = v
+                rec(u + 1)
+                phi[u] = -1
+
+    rec(0)
+    return out
+
+
+def brute_bdsm(n: int, labels, src, dst, query, batch):
+    """O1: (positive set, negative set, charge) by static enumeration on G and G'.
+
+    charge maps each incremental match (sign, phi) to the lowest index among
+    the same-sign updates whose edge is the image of a query edge.
+    """
+    g = {_edge(int(a), int(b)) for a, b in zip(src, dst)}
+    upd: Dict[Tuple[int, int], int] = {}
+    for k, (o, a, b) in enumerate(zip(batch.op, batch.src, batch.dst)):
+        upd[_edge(int(a), int(b))] = k
+    ins = {e for e, k in upd.items() if batch.op[k] > 0}
+    dele = {e for e, k in upd.items() if batch.op[k] < 0}
+    gp = (g - dele) | ins
+    e0 = brute_embeddings(n, labels, g, query)
+    e1 = brute_embeddings(n, labels, gp, query)
+    pos, neg = e1 - e0, e0 - e1
+    qe = [(int(a), int(b)) for a, b in zip(query.src, query.dst)]
+    charge: Dict[Tuple[int, Tuple[int, ...]], int] = {}
+    for sign, s in ((1, pos), (-1, neg)):
+        for phi in s:
+            ks = [upd[_edge(phi[a], phi[b])] for a, b in qe
+                  if _edge(phi[a], phi[b]) in upd and batch.op[upd[_edge(phi[a], phi[b])]] == sign]
+            charge[(sign, phi)] = min(ks)
+    return pos, neg, charge
+
+
+if __name__ == "__main__":  # build only
+    print(build(force="--force" in sys.argv))

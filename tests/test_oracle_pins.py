@@ -1,0 +1,258 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Every test here runs on the CPU. Each pin is independent of the oracle's own
+code: the paper's running example (reconstructed, Sec. I Example 1), a
+brute-force static difference (Def. 1 / Def. 2 written out), networkx's
+subgraph-monomorphism enumerator, textbook closed forms (single edge, triangle
+listing, wedge count from degrees) and invariants of the problem statement.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2401_17018_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _running():
+    with open(os.path.join(GOLD, "running_example.json")) as f:
+        d = json.load(f)
+    e = np.array(d["edges"], np.int32)
+    q = I.pattern_query(d["query"]["labels"], [tuple(x) for x in d["query"]["edges"]])
+    b = I.Batch(np.array(d["batch"]["op"], np.int8), np.array(d["batch"]["src"], np.int32),
+                np.array(d["batch"]["dst"], np.int32))
+    return d, np.array(d["labels"], np.int32), e[:, 0].copy(), e[:, 1].copy(), q, b
+
+
+def _tupset(t, sign=None):
+    return {tuple(int(x) for x in r[2:]) for r in t if sign is None or r[1] == sign}
+
+
+def test_running_example_bdsm():
+    d, lab, s, t, q, b = _running()
+    c, tup = O.bdsm(d["n"], lab, s, t, q, b, want_tuples=True)
+    assert O.totals(c, b.op) == (d["bdsm"]["pos"], d["bdsm"]["neg"])
+    assert c.tolist() == d["bdsm"]["per_update"]
+    assert _tupset(tup, 1) == {tuple(x) for x in d["bdsm"]["pos_tuples"]}
+    # the match quoted in the text exists in G (a static embedding)
+    emb = O.brute_embeddings(d["n"], lab, {(min(a, bb), max(a, bb)) for a, bb in zip(s, t)}, q)
+    assert tuple(d["static_match_in_G"]) in emb
+
+
+def test_running_example_csm_sequence():
+    """One update per batch, applied in order: +4, +2, -2 (Sec. I, Example 1)."""
+    d, lab, s, t, q, b = _running()
+    cs, ct = s.copy(), t.copy()
+    for k in range(len(b)):
+        one = I.Batch(b.op[k:k + 1], b.src[k:k + 1], b.dst[k:k + 1])
+        c, tup = O.bdsm(d["n"], lab, cs, ct, q, one, want_tuples=True)
+        want = d["csm"][k]
+        assert O.totals(c, one.op) == (want["pos"], want["neg"])
+        if "pos_tuples" in want:
+            assert _tupset(tup, 1) == {tuple(x) for x in want["pos_tuples"]}
+        if "neg_tuples" in want:
+            assert _tupset(tup, -1) == {tuple(x) for x in want["neg_tuples"]}
+        cs, ct = I.apply_batch_edges(cs, ct, one)
+    # BDSM is not the concatenation of the CSM results (Sec. I)
+    c, _ = O.bdsm(d["n"], lab, s, t, q, b)
+    assert O.totals(c, b.op) != (4 + 2, 2)
+
+
+def _random_batch(g: I.Graph, seed: int, n_ins: int, n_del: int) -> I.Batch:
+    r = np.random.default_rng(seed)
+    es = set(zip(g.src.tolist(), g.dst.tolist()))
+    non = [(a, bb) for a in range(g.n) for bb in range(a + 1, g.n) if (a, bb) not in es]
+    ni = min(len(non), n_ins)
+    nd = min(len(es), n_del)
+    ins = [non[i] for i in r.choice(len(non), ni, replace=False)] if ni else []
+    el = sorted(es)
+    dl = [el[i] for i in r.choice(len(el), nd, replace=False)] if nd else []
+    ops = [1] * len(ins) + [-1] * len(dl)
+    ed = ins + dl
+    perm = r.permutation(len(ops))
+    flip = r.integers(0, 2, len(ops))
+    src = [ed[i][flip[j]] for j, i in enumerate(perm)]
+    dst = [ed[i][1 - flip[j]] for j, i in enumerate(perm)]
+    return I.Batch(np.array([ops[i] for i in perm], np.int8), np.array(src, np.int32), np.array(dst, np.int32))
+
+
+SMALL_QUERIES = [
+    I.pattern_query([0, 1], [(0, 1)]),
+    I.pattern_query([0, 0, 0], [(0, 1), (1, 2)]),
+    I.pattern_query([1, 0, 1], [(0, 1), (1, 2), (0, 2)]),
+    I.pattern_query([0, 1, 1, 0], [(0, 1), (0, 2), (1, 2), (2, 3)]),
+    I.pattern_query([0, 0, 0, 0], [(0, 1), (1, 2), (2, 3), (3, 0)]),
+]
+
+
+@pytest.mark.parametrize("trial", range(60))
+def test_incremental_equals_static_difference(trial):
+    """O2 (per-update search with charging) == O1 (Emb(G') - Emb(G) and back)."""
+    g = I.random_small_graph(8, 45, 2, 3, trial)
+    b = _random_batch(g, trial, 1 + trial % 4, trial % 3)
+    for q in SMALL_QUERIES:
+        pos, neg, charge = O.brute_bdsm(g.n, g.labels, g.src, g.dst, q, b)
+        c, tup = O.bdsm(g.n, g.labels, g.src, g.dst, q, b, want_tuples=True)
+        want = np.zeros(len(b), np.int64)
+        for (_s, _phi), k in charge.items():
+            want[k] += 1
+        assert np.array_equal(c.astype(np.int64), want)
+        got = {(int(r[1]), tuple(int(x) for x in r[2:])) for r in tup}
+        assert len(got) == len(tup)  # no match found twice
+        assert got == {(1, p) for p in pos} | {(-1, p) for p in neg}
+        for r in tup:  # each row charged to its lowest same-sign update
+            assert charge[(int(r[1]), tuple(int(x) for x in r[2:]))] == r[0]
+
+
+def _nx_embeddings(n, labels, edges, q):
+    nx = pytest.importorskip("networkx")
+    from networkx.algorithms import isomorphism as iso
+    G = nx.Graph()
+    G.add_nodes_from((v, {"l": int(labels[v])}) for v in range(n))
+    G.add_edges_from(edges)
+    P = nx.Graph()
+    P.add_nodes_from((u, {"l": int(q.labels[u])}) for u in range(q.q))
+    P.add_edges_from(zip(q.src.tolist(), q.dst.tolist()))
+    gm = iso.GraphMatcher(G, P, node_match=lambda a, b: a["l"] == b["l"])
+    out = set()
+    for mp in gm.subgraph_monomorphisms_iter():
+        inv = {u: v for v, u in mp.items()}
+        out.add(tuple(inv[u] for u in range(q.q)))
+    return out
+
+
+@pytest.mark.parametrize("trial", range(6))
+def test_against_networkx_monomorphisms(trial):
+    """Static embeddings from networkx (a library routine) differenced on G and G'."""
+    g = I.random_small_graph(30, 18, 3, 11, trial)
+    b = _random_batch(g, 100 + trial, 6, 4)
+    ge = set(zip(g.src.tolist(), g.dst.tolist()))
+    gp = set(ge)
+    for o, s, t in zip(b.op, b.src, b.dst):
+        e = (min(s, t), max(s, t))
+        if o > 0:
+            gp.add(e)
+        else:
+            gp.discard(e)
+    for q in [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)]),
+              I.pattern_query([0, 0, 1, 1], [(0, 1), (1, 2), (2, 3), (3, 0)])]:
+        e0 = _nx_embeddings(g.n, g.labels, ge, q)
+        e1 = _nx_embeddings(g.n, g.labels, gp, q)
+        c, tup = O.bdsm(g.n, g.labels, g.src, g.dst, q, b, want_tuples=True)
+        assert _tupset(tup, 1) == e1 - e0
+        assert _tupset(tup, -1) == e0 - e1
+        assert O.totals(c, b.op) == (len(e1 - e0), len(e0 - e1))
+
+
+def test_single_edge_closed_form():
+    """Q = one edge: each label-compatible update counts once per orientation."""
+    w = I.make_workload("tiny")
+    g = w.graph
+    b = I.workload_batch(w, 200, 50)
+    for la, lb in [(0, 1), (2, 2), (3, 0)]:
+        q = I.pattern_query([la, lb], [(0, 1)])
+        c, _ = O.bdsm(g.n, g.labels, g.src, g.dst, q, b)
+        L = g.labels
+        want = [int(L[s] == la and L[t] == lb) + int(L[t] == la and L[s] == lb) for s, t in zip(b.src, b.dst)]
+        assert c.tolist() == want
+
+
+def _triangles(n, edges):
+    nx = pytest.importorskip("networkx")
+    G = nx.Graph()
+    G.add_nodes_from(range(n))
+    G.add_edges_from(edges)
+    return {tuple(sorted(c)) for c in nx.enumerate_all_cliques(G) if len(c) == 3}
+
+
+def test_unlabelled_triangle_closed_form():
+    """6 embeddings per new / vanished triangle (triangle listing from networkx)."""
+    g = I.random_small_graph(40, 22, 1, 5, 0)
+    b = _random_batch(g, 7, 15, 10)
+    ge = set(zip(g.src.tolist(), g.dst.tolist()))
+    gp = set(ge)
+    for o, s, t in zip(b.op, b.src, b.dst):
+        e = (min(s, t), max(s, t))
+        gp.add(e) if o > 0 else gp.discard(e)
+    t0, t1 = _triangles(g.n, ge), _triangles(g.n, gp)
+    q = I.pattern_query([0, 0, 0], [(0, 1), (1, 2), (0, 2)])
+    c, _ = O.bdsm(g.n, g.labels, g.src, g.dst, q, b)
+    assert O.totals(c, b.op) == (6 * len(t1 - t0), 6 * len(t0 - t1))
+
+
+def test_unlabelled_wedge_closed_form():
+    """Ordered 2-paths: Emb = sum_v d(v)(d(v)-1), so pos - neg is the difference."""
+    w = I.make_workload("tiny")
+    g = w.graph
+    b = I.workload_batch(w, 300, 100)
+    lab0 = np.zeros(g.n, np.int32)
+    q = I.pattern_query([0, 0, 0], [(0, 1), (1, 2)])
+    c, _ = O.bdsm(g.n, lab0, g.src, g.dst, q, b)
+    pos, neg = O.totals(c, b.op)
+    d0 = np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n).astype(np.int64)
+    s1, t1 = I.apply_batch_edges(g.src, g.dst, b)
+    d1 = np.bincount(np.concatenate([s1, t1]), minlength=g.n).astype(np.int64)
+    assert pos - neg == int((d1 * (d1 - 1)).sum() - (d0 * (d0 - 1)).sum())
+
+
+def test_invariants_on_tiny_workload():
+    w = I.make_workload("tiny")
+    g = w.graph
+    b = I.workload_batch(w, 256, 64)
+    q = I.TRIANGLE_WITH_TAIL
+    c, tup = O.bdsm(g.n, g.labels, g.src, g.dst, q, b, want_tuples=True)
+    pos, neg = O.totals(c, b.op)
+    assert pos + neg > 0
+    # count equals the number of distinct rows; per-update sums equal totals
+    rows = {(int(r[1]),) + tuple(int(x) for x in r[2:]) for r in tup}
+    assert len(rows) == len(tup) == pos + neg
+    assert int(c.sum()) == pos + neg
+    # permuting the batch keeps the match sets (charges move with the updates)
+    perm = np.random.default_rng(3).permutation(len(b))
+    bp = I.Batch(b.op[perm], b.dst[perm], b.src[perm])
+    cp, tp = O.bdsm(g.n, g.labels, g.src, g.dst, q, bp, want_tuples=True)
+    assert O.totals(cp, bp.op) == (pos, neg)
+    assert {(int(r[1]),) + tuple(int(x) for x in r[2:]) for r in tp} == rows
+    # round trip: the inverse batch on G' removes exactly what the batch added
+    s1, t1 = I.apply_batch_edges(g.src, g.dst, b)
+    ci, ti = O.bdsm(g.n, g.labels, s1, t1, q, b.inverse(), want_tuples=True)
+    assert _tupset(ti, -1) == _tupset(tup, 1)
+    assert _tupset(ti, 1) == _tupset(tup, -1)
+
+
+@pytest.mark.parametrize("case,bad", [
+    ("dup_same", 3), ("insert_existing", 2), ("delete_missing", 1), ("self_loop", 0), ("bad_id", 2),
+    ("ins_del_same_edge", 2)])
+def test_batch_validation(case, bad):
+    g = I.Graph(6, np.zeros(6, np.int32), np.array([0, 1, 2], np.int32), np.array([1, 2, 3], np.int32))
+    q = I.pattern_query([0, 0], [(0, 1)])
+    ops, src, dst = {
+        "dup_same": ([1, 1, 1, 1], [0, 4, 0, 5], [4, 5, 5, 4]),
+        "insert_existing": ([1, -1, 1], [0, 0, 2], [4, 1, 1]),
+        "delete_missing": ([1, -1, 1], [0, 0, 3], [4, 5, 5]),
+        "self_loop": ([1, 1], [2, 0], [2, 4]),
+        "bad_id": ([1, 1, 1], [0, 1, 9], [4, 4, 0]),
+        "ins_del_same_edge": ([1, 1, -1], [0, 1, 4], [4, 5, 0]),
+    }[case]
+    b = I.Batch(np.array(ops, np.int8), np.array(src, np.int32), np.array(dst, np.int32))
+    with pytest.raises(O.OracleError) as e:
+        O.bdsm(g.n, g.labels, g.src, g.dst, q, b)
+    assert e.value.code == O.EINVAL and e.value.bad_index == bad
+
+
+def test_planted_mistakes_are_caught():
+    """A plausible bug in the charging or view logic changes these pins."""
+    d, lab, s, t, q, b = _running()
+    # ignoring the sign (treating the deletion as an insertion) changes the result
+    b2 = I.Batch(np.array([1, 1, 1], np.int8), b.src, b.dst)
+    with pytest.raises(O.OracleError):
+        O.bdsm(d["n"], lab, s, t, q, b2)  # (4,5) exists: inserting it is invalid
+    # dropping the deletion gives the CSM-like +6 instead of +4
+    b3 = I.Batch(b.op[:2].copy(), b.src[:2].copy(), b.dst[:2].copy())
+    c3, _ = O.bdsm(d["n"], lab, s, t, q, b3)
+    assert O.totals(c3, b3.op) == (6, 0)
