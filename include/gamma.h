@@ -1,0 +1,175 @@
+/*
+ * gamma.h -- C-ABI of libgamma: batch-dynamic subgraph matching (BDSM) on one
+ * GB300 GPU.
+ *
+ * Problem (Sec. II-A, Def. 1, Def. 2 and the Problem Statement): a labelled
+ * undirected data graph G receives a batch of edge insertions and deletions
+ * and becomes G'.  For every registered labelled, connected query graph Q the
+ * library enumerates the incremental matches: embeddings of Q (injective,
+ * label-preserving, every query edge mapped onto a data edge; non-induced)
+ * that are in G' but not in G (positive) or in G but not in G' (negative).
+ * Every such match uses at least one update edge of its own sign and is
+ * charged to exactly one update, the lowest-indexed one among those edges
+ * (Sec. IV-C: a total order over updates so that no match is found twice).
+ *
+ * State machine: create -> load_graph -> register_query* ->
+ *   (apply_batch -> [fetch_matches | update_counts]* -> commit)* -> destroy.
+ * A second apply_batch before commit returns GAMMA_ESTATE.
+ *
+ * Pointers: every input array may be host memory (pageable or pinned) or
+ * device memory of the context's device; the library tells them apart with
+ * cudaPointerGetAttributes and copies host arrays on the context's stream.
+ * Inputs stay owned by the caller and are not retained after a call returns.
+ * Output buffers are owned by the caller.  All calls are synchronous with
+ * respect to the host (they return after their device work has finished).
+ *
+ * Errors: every int-returning call returns GAMMA_OK (0) or a negative code;
+ * gamma_last_error gives a message.  Nothing aborts the process and no call
+ * leaves the graph half-updated: an invalid batch is rejected before the
+ * graph changes.  One context is used by one host thread at a time.
+ */
+#ifndef GAMMA_H
+#define GAMMA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GAMMA_API __attribute__((visibility("default")))
+#else
+#define GAMMA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GAMMA_OK 0
+#define GAMMA_EINVAL (-1)    /* bad argument, graph, query or batch */
+#define GAMMA_ENOMEM (-2)    /* device or host allocation failed */
+#define GAMMA_ESTATE (-3)    /* call not allowed in the current state */
+#define GAMMA_EOVERFLOW (-4) /* match buffer too small; counts still exact */
+#define GAMMA_ETIMEOUT (-5)  /* work budget exceeded; counts incomplete */
+#define GAMMA_ECUDA (-6)     /* CUDA runtime error */
+
+/* option flags */
+#define GAMMA_F_PER_UPDATE 0x1u  /* keep per-update charged counts (gamma_update_counts) */
+#define GAMMA_F_NO_FILTER 0x2u   /* disable the neighbour-label-count candidate filter */
+#define GAMMA_F_PER_QUERY 0x4u   /* plain form: one seed+DFS launch sequence per query */
+#define GAMMA_F_GRAPH 0x8u       /* replay the match phase as a captured CUDA graph */
+
+typedef struct gamma_ctx gamma_ctx;
+
+typedef struct {
+  int device;            /* CUDA device ordinal */
+  void *cuda_stream;     /* cudaStream_t to run on; NULL = a stream owned by the context */
+  uint32_t flags;        /* GAMMA_F_* */
+  uint64_t work_budget;  /* max 32-candidate expansion steps per apply; 0 = unlimited */
+  int warps_per_block;   /* DFS kernel warps per block; 0 = 8 */
+  int frontier_tile;     /* partial matches buffered per DFS level per warp (32..256); 0 = 64 */
+  int steal_grain;       /* level-2 candidates per work item; 0 = 64 */
+} gamma_options;
+
+/* Match rows: row r is rows[r*stride .. r*stride+stride): query id, update
+ * index, sign (+1/-1), then phi(u_0) .. phi(u_{q-1}) in query-vertex order,
+ * then -1 padding.  stride >= 3 + the largest q of the requested queries. */
+typedef struct {
+  int32_t *rows;      /* caller buffer, host or device */
+  int64_t capacity;   /* rows that fit */
+  int32_t stride;     /* int32 per row */
+  int64_t written;    /* out: rows written (<= capacity) */
+  int64_t required;   /* out: rows that exist (written < required => GAMMA_EOVERFLOW) */
+} gamma_matches;
+
+typedef struct {
+  double ms_stage;     /* A1: batch validation + staging into the dynamic CSR */
+  double ms_seed;      /* A2: seeding */
+  double ms_match;     /* A5: DFS extension */
+  double ms_finalize;  /* A6: count reduction and row compaction */
+  double ms_commit;    /* A8: last commit */
+  int64_t seeds;       /* seeds that passed the label and filter tests */
+  int64_t work_items;  /* DFS work items (seeds split by steal_grain) */
+  int64_t touched;     /* vertices whose adjacency the last batch touched */
+  int64_t pool_used;   /* adjacency slots allocated (entries) */
+  int64_t pool_cap;    /* adjacency slots available */
+  int64_t live_edges;  /* directed adjacency entries of the current graph */
+  uint64_t expansions; /* 32-candidate expansion steps of the last apply */
+} gamma_stats;
+
+/* Create a context on options->device (options may be NULL: defaults).
+ * *out receives the context; GAMMA_ECUDA if the device cannot be used. */
+GAMMA_API int gamma_create(const gamma_options *options, gamma_ctx **out);
+
+/* Free all device and host state of ctx (NULL is ignored). */
+GAMMA_API void gamma_destroy(gamma_ctx *ctx);
+
+/* Load the data graph G (Sec. II-A): n vertices with labels[n] (>= 0), m
+ * undirected edges (src[e], dst[e]).  Repeated edges, in either direction,
+ * are merged; a self-loop, an id outside [0, n) or a negative label gives
+ * GAMMA_EINVAL.  Limit: 1 + ceil(log2 n) + ceil(log2(max label + 1)) <= 32
+ * (vertex id and label are packed into one 32-bit adjacency key); labels < 256.
+ * Replaces any previously loaded graph and forgets registered queries. */
+GAMMA_API int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels,
+                     int64_t m, const int32_t *src, const int32_t *dst);
+
+/* Register a query graph Q (Sec. II-A): 2 <= q <= 16 vertices with
+ * qlabels[q], eq undirected edges (qsrc[e], qdst[e]) in [0, q).  Q must be
+ * connected and simple.  The host builds one matching order per query edge
+ * and orientation (Alg. 1 input pi; Sec. IV-C).  *out_qid receives the id. */
+GAMMA_API int gamma_register_query(gamma_ctx *ctx, int32_t q, const int32_t *qlabels,
+                         int32_t eq, const int32_t *qsrc, const int32_t *qdst,
+                         int32_t *out_qid);
+
+/* Apply one update batch Delta-B (Def. 1) of b updates: op[k] = +1 inserts
+ * edge (src[k], dst[k]), -1 deletes it; the position k is the update's index
+ * in the total order used for charging.  The batch is rejected with
+ * GAMMA_EINVAL, leaving G unchanged, if an update has an id out of range, a
+ * self-loop, an op other than +1/-1, repeats an edge of an earlier update,
+ * inserts an existing edge or deletes a missing one (the message names the
+ * smallest offending index).  Otherwise G' is staged and, for each of the nq
+ * queries qids[j], out_pos[j] / out_neg[j] (host arrays) receive the number
+ * of positive / negative incremental matches.  With opt_out non-NULL the
+ * match rows are written too (GAMMA_EOVERFLOW when they do not fit; the
+ * counts are exact regardless).  GAMMA_ETIMEOUT: work budget exceeded. */
+GAMMA_API int gamma_apply_batch(gamma_ctx *ctx, int64_t b, const int8_t *op,
+                      const int32_t *src, const int32_t *dst,
+                      int32_t nq, const int32_t *qids,
+                      uint64_t *out_pos, uint64_t *out_neg,
+                      gamma_matches *opt_out);
+
+/* Re-run the matching of the staged batch and write its match rows into out
+ * (after GAMMA_EOVERFLOW, with a larger buffer).  GAMMA_ESTATE if no batch is
+ * staged. */
+GAMMA_API int gamma_fetch_matches(gamma_ctx *ctx, gamma_matches *out);
+
+/* Per-update charged counts of the staged batch for the j-th requested query
+ * (0 <= j < nq of the last apply_batch): out[k] (host, b entries) = number of
+ * incremental matches charged to update k.  Needs GAMMA_F_PER_UPDATE. */
+GAMMA_API int gamma_update_counts(gamma_ctx *ctx, int32_t j, uint64_t *out);
+
+/* Make G' the current graph: drop deleted edges, clear batch tags (A8).
+ * GAMMA_ESTATE if no batch is staged. */
+GAMMA_API int gamma_commit(gamma_ctx *ctx);
+
+/* Copy the current adjacency to host arrays, for checking the dynamic CSR
+ * (A1/A8) against a host model.  While a batch is staged this is the union
+ * graph G u G'.  off[n+1] (int64) delimits each vertex's list; for entry i,
+ * nbr[i] is the neighbour id and tag[i] is -1 for an edge the staged batch
+ * does not touch, else 2 * (update index) + (1 for a deletion).  Lists are in
+ * the library's order (neighbour label, then id).  cap = room in nbr/tag;
+ * returns GAMMA_EOVERFLOW when the entries do not fit (off is still filled). */
+GAMMA_API int gamma_export_adjacency(gamma_ctx *ctx, int64_t *off, int32_t *nbr, int32_t *tag, int64_t cap);
+
+/* Timings and sizes of the last apply/commit. */
+GAMMA_API int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out);
+
+/* Change flags / tuning knobs between batches (fields as in gamma_options;
+ * 0 keeps the current value for the three tuning fields). */
+GAMMA_API int gamma_set_options(gamma_ctx *ctx, const gamma_options *options);
+
+/* Message for the last error on ctx (never NULL; "" when none). */
+GAMMA_API const char *gamma_last_error(gamma_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAMMA_H */

@@ -1,0 +1,813 @@
+// gm_api.cu -- the C-ABI of libgamma (include/gamma.h): context and state
+// machine, host planner (matching orders, Alg. 1 input pi), buffer management
+// and the launch sequence of one batch: stage (A1) -> seed (A2) -> DFS (A5)
+// with row compaction (A6) -> counts to the host; commit (A8) separately.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "gm_graph.cuh"
+
+static thread_local char g_cuda_msg[512];
+
+int gm_cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+  snprintf(g_cuda_msg, sizeof(g_cuda_msg), "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e),
+           cudaGetErrorString(e), what, file, line);
+  return (e == cudaErrorMemoryAllocation) ? GAMMA_ENOMEM : GAMMA_ECUDA;
+}
+
+namespace {
+
+struct HostQuery {
+  int q = 0;
+  std::vector<int32_t> lab;
+  std::vector<std::pair<int, int>> edges;
+  std::vector<Plan> plans;
+  bool never = false;  // a label absent from G: no embedding can exist
+};
+
+template <class T>
+int ensure(T *&p, int64_t &cap, int64_t need) {
+  if (need <= cap && p) return GAMMA_OK;
+  if (p) cudaFree(p);
+  p = nullptr;
+  int64_t c = std::max<int64_t>(need, 1);
+  cudaError_t e = cudaMalloc((void **)&p, sizeof(T) * (size_t)c);
+  if (e != cudaSuccess) { cap = 0; p = nullptr; return gm_cuda_fail(e, "cudaMalloc", __FILE__, __LINE__); }
+  cap = c;
+  return GAMMA_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct gamma_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint32_t flags = 0;
+  uint64_t budget = 0;
+  int wpb = 8, tile = 64, grain = 64;
+  int num_sms = 0;
+  std::string err;
+
+  // graph
+  bool loaded = false;
+  int32_t n = 0;
+  int idb = 1, nlab = 1, nlfw = 4;
+  int32_t *d_label = nullptr;
+  uint2 *d_adj = nullptr;
+  uint32_t *d_cap = nullptr, *d_col = nullptr, *d_etag = nullptr;
+  uint8_t *d_nlf = nullptr;
+  uint32_t pool_cap = 0;
+  uint64_t pool_top = 0;
+  int64_t live = 0;
+  std::vector<int64_t> label_freq;
+
+  // queries
+  std::vector<HostQuery> queries;
+
+  // batch
+  StageBufs sb;
+  int64_t in_cap = 0;
+  int8_t *d_in_op = nullptr;
+  int32_t *d_in_src = nullptr, *d_in_dst = nullptr;
+  bool staged = false;
+  int64_t b = 0;
+  std::vector<int32_t> qids;
+
+  // match
+  Plan *d_plans = nullptr;
+  int64_t plans_cap = 0;
+  uint32_t *d_pair_off = nullptr;
+  int64_t pair_off_cap = 0;
+  uint16_t *d_pair_plans = nullptr;
+  int64_t pair_plans_cap = 0;
+  std::vector<int32_t> plan_key;  // qids + form the device tables were built for
+  std::vector<int> group_nplans;
+  int nplans = 0, maxq = 2;
+  WorkItem *d_items = nullptr;
+  int64_t items_cap = 0;
+  uint64_t *d_cnt = nullptr;
+  int64_t cnt_cap = 0;
+  uint64_t *d_per_upd = nullptr;
+  int64_t per_upd_cap = 0;
+  int32_t *d_rows = nullptr;
+  int64_t rows_cap = 0;
+
+  GmStatus *d_st = nullptr;
+  GmStatus *h_st = nullptr;       // pinned
+  uint64_t *h_cnt = nullptr;      // pinned
+  int64_t h_cnt_cap = 0;
+  cudaEvent_t ev[8] = {};
+  gamma_stats stats = {};
+
+  GraphDev gd() const {
+    GraphDev g;
+    g.label = d_label; g.adj = d_adj; g.cap = d_cap; g.col = d_col; g.etag = d_etag; g.nlf = d_nlf;
+    g.n = n; g.idb = idb; g.nlab = nlab; g.nlfw = nlfw;
+    g.idmask = (idb >= 32) ? 0xffffffffu : ((1u << idb) - 1u);
+    g.pool_cap = pool_cap;
+    return g;
+  }
+
+  int fail(int code, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+  int cuda_fail(int code) {
+    err = g_cuda_msg;
+    return code;
+  }
+};
+
+#define CK(call)                                        \
+  do {                                                  \
+    int rc__ = (call);                                  \
+    if (rc__ != GAMMA_OK) return ctx->cuda_fail(rc__);  \
+  } while (0)
+#define CKC(call) CK(((call) == cudaSuccess) ? GAMMA_OK : gm_cuda_fail(cudaGetLastError(), #call, __FILE__, __LINE__))
+
+namespace {
+
+void free_graph(gamma_ctx *ctx) {
+  cudaFree(ctx->d_label); cudaFree(ctx->d_adj); cudaFree(ctx->d_cap);
+  cudaFree(ctx->d_col); cudaFree(ctx->d_etag); cudaFree(ctx->d_nlf);
+  ctx->d_label = nullptr; ctx->d_adj = nullptr; ctx->d_cap = nullptr;
+  ctx->d_col = nullptr; ctx->d_etag = nullptr; ctx->d_nlf = nullptr;
+  ctx->loaded = false;
+  ctx->staged = false;
+}
+
+int bits_for(int64_t x) {  // bits to represent values 0..x-1 (>= 1)
+  int b = 1;
+  while (b < 63 && ((int64_t)1 << b) < x) b++;
+  return b;
+}
+
+// matching order for one seeded query edge (Alg. 1 input pi; Sec. IV-C: more
+// selective vertices first): every next vertex has an already placed query
+// neighbour; prefer more placed neighbours, then higher degree, then a rarer
+// label in G, then the smaller id.
+void make_plan(const HostQuery &Q, int qid, int a, int b, const std::vector<int64_t> &freq, Plan &P) {
+  const int q = Q.q;
+  std::vector<std::vector<char>> adjq(q, std::vector<char>(q, 0));
+  std::vector<int> deg(q, 0);
+  for (auto &e : Q.edges) { adjq[e.first][e.second] = adjq[e.second][e.first] = 1; deg[e.first]++; deg[e.second]++; }
+  std::vector<int> order = {a, b};
+  std::vector<char> placed(q, 0);
+  placed[a] = placed[b] = 1;
+  while ((int)order.size() < q) {
+    int best = -1;
+    long long bk[4] = {0, 0, 0, 0};
+    for (int u = 0; u < q; u++) {
+      if (placed[u]) continue;
+      int nb = 0;
+      for (int w : order) nb += adjq[u][w];
+      if (!nb) continue;
+      long long f = (Q.lab[u] < (int)freq.size()) ? freq[Q.lab[u]] : 0;
+      long long key[4] = {nb, deg[u], -f, -u};
+      if (best < 0 || std::lexicographical_compare(bk, bk + 4, key, key + 4)) {
+        best = u;
+        memcpy(bk, key, sizeof(bk));
+      }
+    }
+    order.push_back(best);
+    placed[best] = 1;
+  }
+  memset(&P, 0, sizeof(P));
+  P.q = q;
+  P.qid = qid;
+  for (int l = 0; l < q; l++) {
+    int u = order[l];
+    P.qv[l] = (int8_t)u;
+    P.lab[l] = Q.lab[u];
+    uint16_t bw = 0, sl = 0;
+    for (int k = 0; k < l; k++) {
+      if (adjq[u][order[k]]) bw |= (uint16_t)(1u << k);
+      if (Q.lab[order[k]] == Q.lab[u]) sl |= (uint16_t)(1u << k);
+    }
+    P.bwd[l] = bw;
+    P.samelab[l] = sl;
+    // neighbour-label counts of u in Q (Sec. IV-B: |N^l(v)| >= |N^l(u)|)
+    std::vector<std::pair<int, int>> req;
+    for (int w = 0; w < q; w++) {
+      if (!adjq[u][w]) continue;
+      bool found = false;
+      for (auto &r : req) if (r.first == Q.lab[w]) { r.second++; found = true; }
+      if (!found) req.push_back({Q.lab[w], 1});
+    }
+    P.nreq[l] = (uint8_t)req.size();
+    for (size_t r = 0; r < req.size(); r++) {
+      P.req_lab[l][r] = (uint8_t)req[r].first;
+      P.req_cnt[l][r] = (uint8_t)req[r].second;
+    }
+  }
+}
+
+// Plan table for one call: all plans of the requested queries (qslot = the
+// query's position in the call), plus one (L(pi[0]), L(pi[1])) -> plans index
+// per launch group (one group in the batched form, one per query in the
+// per-query form).  Uploaded once; reused while the request is unchanged.
+int build_tables(gamma_ctx *ctx, const std::vector<int32_t> &qids, bool per_query) {
+  std::vector<int32_t> key(qids);
+  key.push_back(per_query ? -2 : -1);
+  key.push_back((int32_t)ctx->nlab);
+  if (key == ctx->plan_key && ctx->d_plans) return GAMMA_OK;
+  const int nq = (int)qids.size();
+  std::vector<Plan> table;
+  std::vector<int> qstart(nq + 1, 0);
+  int maxq = 2;
+  for (int j = 0; j < nq; j++) {
+    qstart[j] = (int)table.size();
+    const HostQuery &Q = ctx->queries[qids[j]];
+    if (!Q.never) {
+      for (const Plan &p0 : Q.plans) {
+        Plan p = p0;
+        p.qslot = j;
+        table.push_back(p);
+        maxq = std::max(maxq, p.q);
+      }
+    }
+  }
+  qstart[nq] = (int)table.size();
+  if (table.size() > 65535) return ctx->fail(GAMMA_EINVAL, "too many matching plans in one call (%zu > 65535)", table.size());
+  const int np = ctx->nlab * ctx->nlab;
+  const int ngroups = per_query ? nq : 1;
+  std::vector<uint32_t> off((size_t)ngroups * (np + 1), 0);
+  std::vector<uint16_t> pp;
+  ctx->group_nplans.assign(ngroups, 0);
+  for (int gi = 0; gi < ngroups; gi++) {
+    int p0 = per_query ? qstart[gi] : 0, p1 = per_query ? qstart[gi + 1] : (int)table.size();
+    uint32_t *o = off.data() + (size_t)gi * (np + 1);
+    for (int i = p0; i < p1; i++) o[table[i].lab[0] * ctx->nlab + table[i].lab[1] + 1]++;
+    for (int i = 0; i < np; i++) o[i + 1] += o[i];
+    size_t base = pp.size();
+    pp.resize(base + (p1 - p0));
+    std::vector<uint32_t> fill(o, o + np);
+    for (int i = p0; i < p1; i++) pp[base + fill[table[i].lab[0] * ctx->nlab + table[i].lab[1]]++] = (uint16_t)i;
+    for (int i = 0; i <= np; i++) o[i] += (uint32_t)base;
+    ctx->group_nplans[gi] = p1 - p0;
+  }
+  if (pp.empty()) pp.push_back(0);
+  CK(ensure(ctx->d_plans, ctx->plans_cap, (int64_t)std::max<size_t>(table.size(), 1)));
+  CK(ensure(ctx->d_pair_off, ctx->pair_off_cap, (int64_t)off.size()));
+  CK(ensure(ctx->d_pair_plans, ctx->pair_plans_cap, (int64_t)pp.size()));
+  if (!table.empty())
+    CKC(cudaMemcpyAsync(ctx->d_plans, table.data(), sizeof(Plan) * table.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CKC(cudaMemcpyAsync(ctx->d_pair_off, off.data(), sizeof(uint32_t) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CKC(cudaMemcpyAsync(ctx->d_pair_plans, pp.data(), sizeof(uint16_t) * pp.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CKC(cudaStreamSynchronize(ctx->stream));  // host vectors go out of scope
+  ctx->nplans = (int)table.size();
+  ctx->maxq = maxq;
+  ctx->plan_key = key;
+  return GAMMA_OK;
+}
+
+int grow_pool(gamma_ctx *ctx, uint64_t need) {
+  uint64_t cap = std::max<uint64_t>((uint64_t)(ctx->pool_cap * 1.5), need + (need >> 2) + 1024);
+  if (cap >= (1ull << 32) - 64) cap = (1ull << 32) - 64;
+  if (cap <= ctx->pool_cap) return ctx->fail(GAMMA_ENOMEM, "adjacency pool cannot grow past 2^32 slots");
+  uint32_t *col = nullptr, *etag = nullptr;
+  CKC(cudaMalloc((void **)&col, sizeof(uint32_t) * cap));
+  CKC(cudaMalloc((void **)&etag, sizeof(uint32_t) * cap));
+  CKC(cudaMemcpyAsync(col, ctx->d_col, sizeof(uint32_t) * ctx->pool_top, cudaMemcpyDeviceToDevice, ctx->stream));
+  CKC(cudaMemcpyAsync(etag, ctx->d_etag, sizeof(uint32_t) * ctx->pool_top, cudaMemcpyDeviceToDevice, ctx->stream));
+  CKC(cudaStreamSynchronize(ctx->stream));
+  cudaFree(ctx->d_col);
+  cudaFree(ctx->d_etag);
+  ctx->d_col = col;
+  ctx->d_etag = etag;
+  ctx->pool_cap = (uint32_t)cap;
+  return GAMMA_OK;
+}
+
+void reset_status_host(gamma_ctx *ctx) {
+  memset(ctx->h_st, 0, sizeof(GmStatus));
+  ctx->h_st->bad_index = INT64_MAX;
+  ctx->h_st->pool_top = (uint32_t)ctx->pool_top;
+}
+
+float ev_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) { cudaGetLastError(); return 0.f; }
+  return ms;
+}
+
+// seed + DFS for the staged batch; rows may be null.  Leaves counts in
+// ctx->h_cnt and the status in ctx->h_st.
+int run_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_stride) {
+  const int nq = (int)ctx->qids.size();
+  const int64_t b = ctx->b;
+  const bool per_query = (ctx->flags & GAMMA_F_PER_QUERY) != 0;
+  CK(build_tables(ctx, ctx->qids, per_query));
+  CK(ensure(ctx->d_cnt, ctx->cnt_cap, (int64_t)2 * std::max(nq, 1)));
+  if (ctx->flags & GAMMA_F_PER_UPDATE) CK(ensure(ctx->d_per_upd, ctx->per_upd_cap, std::max<int64_t>((int64_t)nq * b, 1)));
+  if (ctx->h_cnt_cap < 2 * std::max(nq, 1)) {
+    if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
+    CKC(cudaMallocHost((void **)&ctx->h_cnt, sizeof(uint64_t) * 2 * std::max(nq, 1)));
+    ctx->h_cnt_cap = 2 * std::max(nq, 1);
+  }
+  if (ctx->items_cap == 0) CK(ensure(ctx->d_items, ctx->items_cap, std::max<int64_t>(1 << 20, 8 * b)));
+  for (int attempt = 0; attempt < 4; attempt++) {
+    cudaStream_t s = ctx->stream;
+    CKC(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(uint64_t) * 2 * std::max(nq, 1), s));
+    if (ctx->flags & GAMMA_F_PER_UPDATE)
+      CKC(cudaMemsetAsync(ctx->d_per_upd, 0, sizeof(uint64_t) * std::max<int64_t>((int64_t)nq * b, 1), s));
+    // clear the match part of the status (err/abort and nseeds..rows)
+    CKC(cudaMemsetAsync(&ctx->d_st->err, 0, 2 * sizeof(int32_t), s));
+    CKC(cudaMemsetAsync(&ctx->d_st->nseeds, 0, 5 * sizeof(uint64_t), s));
+    CKC(cudaEventRecord(ctx->ev[2], s));
+    MatchArgs a;
+    a.g = ctx->gd();
+    a.cu = ctx->sb.cu; a.cv = ctx->sb.cv; a.op = ctx->sb.cop; a.b = b;
+    a.grain = ctx->grain;
+    a.items = ctx->d_items; a.item_cap = (uint64_t)ctx->items_cap;
+    a.cnt = ctx->d_cnt;
+    a.per_upd = (ctx->flags & GAMMA_F_PER_UPDATE) ? ctx->d_per_upd : nullptr;
+    a.use_filter = (ctx->flags & GAMMA_F_NO_FILTER) ? 0 : 1;
+    a.rows = rows_dev; a.row_cap = row_cap; a.row_stride = row_stride;
+    a.budget = ctx->budget;
+    a.tile = ctx->tile;
+    a.warps_per_block = ctx->wpb;
+    a.st = ctx->d_st;
+    a.plans = ctx->d_plans; a.nplans = ctx->nplans;
+    a.pair_plans = ctx->d_pair_plans;
+    a.nlev = std::max(1, ctx->maxq - 3);
+    const int np = ctx->nlab * ctx->nlab;
+    const int ngroups = per_query ? nq : 1;
+    bool seeded = false;
+    for (int gi = 0; gi < ngroups; gi++) {
+      if (ctx->group_nplans[gi] == 0) continue;
+      a.pair_off = ctx->d_pair_off + (size_t)gi * (np + 1);
+      if (per_query) CK(gm_begin_group(ctx->d_st, s));
+      CK(gm_seed(a, s));
+      if (!per_query) { CKC(cudaEventRecord(ctx->ev[3], s)); seeded = true; }
+      CK(gm_dfs(a, ctx->num_sms, s));
+    }
+    if (!seeded) CKC(cudaEventRecord(ctx->ev[3], s));
+    CKC(cudaEventRecord(ctx->ev[4], s));
+    CKC(cudaMemcpyAsync(ctx->h_cnt, ctx->d_cnt, sizeof(uint64_t) * 2 * std::max(nq, 1), cudaMemcpyDeviceToHost, s));
+    CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
+    CKC(cudaEventRecord(ctx->ev[5], s));
+    CKC(cudaStreamSynchronize(s));
+    GmStatus &st = *ctx->h_st;
+    if (st.err == 0 && st.nitems > (uint64_t)ctx->items_cap) {
+      int64_t need = (int64_t)(st.nitems + (st.nitems >> 2) + 1024);
+      ctx->items_cap = 0;
+      CK(ensure(ctx->d_items, ctx->items_cap, need));
+      continue;  // redo with room for every item
+    }
+    ctx->stats.ms_seed = ev_ms(ctx->ev[2], ctx->ev[3]);
+    ctx->stats.ms_match = ev_ms(ctx->ev[3], ctx->ev[4]);
+    ctx->stats.ms_finalize = ev_ms(ctx->ev[4], ctx->ev[5]);
+    ctx->stats.seeds = (int64_t)st.nseeds;
+    ctx->stats.work_items = (int64_t)st.nitems;
+    ctx->stats.expansions = st.expansions;
+    return GAMMA_OK;
+  }
+  return ctx->fail(GAMMA_ENOMEM, "work item buffer kept overflowing");
+}
+
+int copy_rows_out(gamma_ctx *ctx, gamma_matches *out, bool dev_rows) {
+  uint64_t produced = ctx->h_st->rows;
+  int64_t written = (int64_t)std::min<uint64_t>(produced, (uint64_t)out->capacity);
+  if (!dev_rows && written > 0)
+    CKC(cudaMemcpy(out->rows, ctx->d_rows, sizeof(int32_t) * (size_t)written * out->stride, cudaMemcpyDeviceToHost));
+  out->written = written;
+  out->required = (int64_t)produced;
+  return (int64_t)produced > out->capacity ? GAMMA_EOVERFLOW : GAMMA_OK;
+}
+
+int match_with_rows(gamma_ctx *ctx, gamma_matches *out) {
+  if (!out) return run_match(ctx, nullptr, 0, 0);
+  if (out->capacity < 0 || (out->capacity > 0 && !out->rows)) return ctx->fail(GAMMA_EINVAL, "bad gamma_matches buffer");
+  int need_stride = 3 + 2;
+  for (int32_t id : ctx->qids) need_stride = std::max(need_stride, 3 + ctx->queries[id].q);
+  if (out->stride < need_stride) return ctx->fail(GAMMA_EINVAL, "gamma_matches.stride %d < %d", out->stride, need_stride);
+  bool dev = is_device_ptr(out->rows);
+  int32_t *rows = out->rows;
+  if (!dev) {
+    CK(ensure(ctx->d_rows, ctx->rows_cap, std::max<int64_t>(out->capacity * out->stride, 1)));
+    rows = ctx->d_rows;
+  }
+  int rc = run_match(ctx, rows, (uint64_t)out->capacity, out->stride);
+  if (rc) return rc;
+  if (ctx->h_st->err) return GAMMA_OK;  // reported by the caller
+  return copy_rows_out(ctx, out, dev);
+}
+
+}  // namespace
+
+// ==========================================================================
+// C-ABI
+// ==========================================================================
+extern "C" {
+
+int gamma_create(const gamma_options *options, gamma_ctx **out) {
+  if (!out) return GAMMA_EINVAL;
+  *out = nullptr;
+  gamma_options o;
+  memset(&o, 0, sizeof(o));
+  if (options) o = *options;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
+    cudaGetLastError();
+    return GAMMA_ECUDA;
+  }
+  if (cudaSetDevice(o.device) != cudaSuccess) return GAMMA_ECUDA;
+  gamma_ctx *ctx = new gamma_ctx();
+  ctx->device = o.device;
+  ctx->flags = o.flags;
+  ctx->budget = o.work_budget;
+  if (o.warps_per_block > 0) ctx->wpb = o.warps_per_block;
+  if (o.frontier_tile > 0) ctx->tile = o.frontier_tile;
+  if (o.steal_grain > 0) ctx->grain = o.steal_grain;
+  if (ctx->tile < 32 || ctx->tile > 4096 || ctx->wpb > 32) { delete ctx; return GAMMA_EINVAL; }
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, o.device);
+  if (o.cuda_stream) {
+    ctx->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return GAMMA_ECUDA; }
+    ctx->own_stream = true;
+  }
+  if (cudaMalloc((void **)&ctx->d_st, sizeof(GmStatus)) != cudaSuccess ||
+      cudaMallocHost((void **)&ctx->h_st, sizeof(GmStatus)) != cudaSuccess) {
+    gamma_destroy(ctx);
+    return GAMMA_ENOMEM;
+  }
+  for (auto &e : ctx->ev) cudaEventCreate(&e);
+  *out = ctx;
+  return GAMMA_OK;
+}
+
+void gamma_destroy(gamma_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_graph(ctx);
+  StageBufs &sb = ctx->sb;
+  void *ps[] = {sb.cu, sb.cv, sb.cop, sb.keys, sb.tk, sb.vals, sb.tv, sb.head, sb.gid, sb.gv, sb.gstart,
+                sb.gins, sb.greloc, sb.bkeys, ctx->d_in_op, ctx->d_in_src, ctx->d_in_dst, ctx->d_plans,
+                ctx->d_pair_off, ctx->d_pair_plans, ctx->d_items, ctx->d_cnt, ctx->d_per_upd, ctx->d_rows,
+                ctx->d_st};
+  for (void *p : ps) if (p) cudaFree(p);
+  if (ctx->h_st) cudaFreeHost(ctx->h_st);
+  if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
+  for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char *gamma_last_error(gamma_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int gamma_set_options(gamma_ctx *ctx, const gamma_options *o) {
+  if (!ctx || !o) return GAMMA_EINVAL;
+  if (o->frontier_tile && (o->frontier_tile < 32 || o->frontier_tile > 4096))
+    return ctx->fail(GAMMA_EINVAL, "frontier_tile must be in [32, 4096]");
+  if (o->warps_per_block < 0 || o->warps_per_block > 32) return ctx->fail(GAMMA_EINVAL, "warps_per_block must be in [1, 32]");
+  ctx->flags = o->flags;
+  ctx->budget = o->work_budget;
+  if (o->warps_per_block) ctx->wpb = o->warps_per_block;
+  if (o->frontier_tile) ctx->tile = o->frontier_tile;
+  if (o->steal_grain) ctx->grain = o->steal_grain;
+  ctx->plan_key.clear();
+  return GAMMA_OK;
+}
+
+int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m, const int32_t *src,
+                     const int32_t *dst) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (n <= 0 || m < 0 || !labels || (m > 0 && (!src || !dst)))
+    return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: bad sizes or null arrays");
+  if (m > ((int64_t)1 << 31) - 1) return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: too many edges");
+  cudaSetDevice(ctx->device);
+  free_graph(ctx);
+  ctx->queries.clear();
+  ctx->plan_key.clear();
+  cudaStream_t s = ctx->stream;
+  // device copies of the inputs
+  const int32_t *dl = labels, *ds = src, *dd = dst;
+  int32_t *ts = nullptr, *td = nullptr;
+  CKC(cudaMalloc((void **)&ctx->d_label, sizeof(int32_t) * n));
+  CKC(cudaMemcpyAsync(ctx->d_label, labels, sizeof(int32_t) * n, cudaMemcpyDefault, s));
+  dl = ctx->d_label;
+  if (m > 0 && !is_device_ptr(src)) {
+    CKC(cudaMalloc((void **)&ts, sizeof(int32_t) * m));
+    CKC(cudaMemcpyAsync(ts, src, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    ds = ts;
+  }
+  if (m > 0 && !is_device_ptr(dst)) {
+    CKC(cudaMalloc((void **)&td, sizeof(int32_t) * m));
+    CKC(cudaMemcpyAsync(td, dst, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    dd = td;
+  }
+  reset_status_host(ctx);
+  CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
+  CK(gm_load_validate(dl, n, ds, dd, m, ctx->d_st, s));
+  CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
+  CKC(cudaStreamSynchronize(s));
+  if (ctx->h_st->err) {
+    cudaFree(ts); cudaFree(td);
+    free_graph(ctx);
+    if (ctx->h_st->bad_index != INT64_MAX)
+      return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: edge %lld has an id out of range or is a self-loop",
+                       (long long)ctx->h_st->bad_index);
+    return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: negative vertex label");
+  }
+  if (ctx->h_st->max_label > 255) {
+    cudaFree(ts); cudaFree(td);
+    free_graph(ctx);
+    return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: vertex labels must be < 256");
+  }
+  ctx->n = n;
+  ctx->nlab = (int)ctx->h_st->max_label + 1;
+  ctx->idb = bits_for(n);
+  int lb = bits_for(ctx->nlab);
+  if (1 + ctx->idb + lb > 32) {
+    cudaFree(ts); cudaFree(td);
+    free_graph(ctx);
+    return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: %d vertex-id bits + %d label bits + 1 exceed 32", ctx->idb, lb);
+  }
+  ctx->nlfw = (ctx->nlab + 3) & ~3;
+  CKC(cudaMalloc((void **)&ctx->d_adj, sizeof(uint2) * n));
+  CKC(cudaMalloc((void **)&ctx->d_cap, sizeof(uint32_t) * n));
+  CKC(cudaMalloc((void **)&ctx->d_nlf, (size_t)n * ctx->nlfw));
+  CKC(cudaMemsetAsync(ctx->d_nlf, 0, (size_t)n * ctx->nlfw, s));
+  uint32_t pool_cap = 0;
+  GraphDev g = ctx->gd();
+  CK(gm_load_build(g, ds, dd, m, &ctx->d_col, &ctx->d_etag, &pool_cap, 1.25, (uint64_t)1 << 20, ctx->d_st,
+                   ctx->h_st, s));
+  ctx->pool_cap = pool_cap;
+  ctx->pool_top = ctx->h_st->pool_top;
+  g = ctx->gd();
+  CK(gm_nlf(g, nullptr, nullptr, (uint32_t)n, s));
+  // live entries and label histogram
+  std::vector<int32_t> hl(n);
+  CKC(cudaMemcpyAsync(hl.data(), ctx->d_label, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  std::vector<uint2> hadj;
+  CKC(cudaStreamSynchronize(s));
+  cudaFree(ts);
+  cudaFree(td);
+  ctx->label_freq.assign(ctx->nlab, 0);
+  for (int32_t v = 0; v < n; v++) ctx->label_freq[hl[v]]++;
+  // live directed entries = sum of list lengths
+  {
+    hadj.resize(n);
+    CKC(cudaMemcpy(hadj.data(), ctx->d_adj, sizeof(uint2) * n, cudaMemcpyDeviceToHost));
+    int64_t live = 0;
+    for (auto &a : hadj) live += a.y;
+    ctx->live = live;
+  }
+  ctx->loaded = true;
+  ctx->staged = false;
+  return GAMMA_OK;
+}
+
+int gamma_register_query(gamma_ctx *ctx, int32_t q, const int32_t *qlabels, int32_t eq, const int32_t *qsrc,
+                         const int32_t *qdst, int32_t *out_qid) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "gamma_register_query: no graph loaded");
+  if (q < 2 || q > GM_MAXQ || eq < q - 1 || eq > q * (q - 1) / 2 || !qlabels || !qsrc || !qdst || !out_qid)
+    return ctx->fail(GAMMA_EINVAL, "gamma_register_query: need 2 <= q <= %d and a connected simple edge list", GM_MAXQ);
+  HostQuery Q;
+  Q.q = q;
+  Q.lab.assign(qlabels, qlabels + q);
+  std::vector<std::vector<char>> adjq(q, std::vector<char>(q, 0));
+  for (int e = 0; e < eq; e++) {
+    int a = qsrc[e], b = qdst[e];
+    if (a < 0 || a >= q || b < 0 || b >= q || a == b || adjq[a][b])
+      return ctx->fail(GAMMA_EINVAL, "gamma_register_query: edge %d is out of range, a self-loop or repeated", e);
+    adjq[a][b] = adjq[b][a] = 1;
+    Q.edges.push_back({a, b});
+  }
+  for (int u = 0; u < q; u++) {
+    if (Q.lab[u] < 0) return ctx->fail(GAMMA_EINVAL, "gamma_register_query: negative label");
+    if (Q.lab[u] >= ctx->nlab) Q.never = true;
+  }
+  // connectivity
+  std::vector<int> stack = {0};
+  std::vector<char> seen(q, 0);
+  seen[0] = 1;
+  while (!stack.empty()) {
+    int u = stack.back();
+    stack.pop_back();
+    for (int w = 0; w < q; w++) if (adjq[u][w] && !seen[w]) { seen[w] = 1; stack.push_back(w); }
+  }
+  for (int u = 0; u < q; u++) if (!seen[u]) return ctx->fail(GAMMA_EINVAL, "gamma_register_query: query is not connected");
+  int qid = (int)ctx->queries.size();
+  if (!Q.never) {
+    for (auto &e : Q.edges) {
+      for (int o = 0; o < 2; o++) {
+        Plan P;
+        make_plan(Q, qid, o ? e.second : e.first, o ? e.first : e.second, ctx->label_freq, P);
+        Q.plans.push_back(P);
+      }
+    }
+  }
+  ctx->queries.push_back(Q);
+  *out_qid = qid;
+  return GAMMA_OK;
+}
+
+int gamma_apply_batch(gamma_ctx *ctx, int64_t b, const int8_t *op, const int32_t *src, const int32_t *dst,
+                      int32_t nq, const int32_t *qids, uint64_t *out_pos, uint64_t *out_neg,
+                      gamma_matches *opt_out) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "gamma_apply_batch: no graph loaded");
+  if (ctx->staged) return ctx->fail(GAMMA_ESTATE, "gamma_apply_batch: previous batch not committed");
+  if (b < 0 || b >= ((int64_t)1 << 31) || nq < 0 || (b > 0 && (!op || !src || !dst)) ||
+      (nq > 0 && (!qids || !out_pos || !out_neg)))
+    return ctx->fail(GAMMA_EINVAL, "gamma_apply_batch: bad sizes or null arrays");
+  for (int j = 0; j < nq; j++)
+    if (qids[j] < 0 || qids[j] >= (int)ctx->queries.size())
+      return ctx->fail(GAMMA_EINVAL, "gamma_apply_batch: unknown query id %d", qids[j]);
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  StageBufs &sb = ctx->sb;
+  if (b > sb.cap) {
+    int64_t c = std::max<int64_t>(b, 1024);
+    void *ps[] = {sb.cu, sb.cv, sb.cop, sb.keys, sb.tk, sb.vals, sb.tv, sb.head, sb.gid, sb.gv, sb.gstart,
+                  sb.gins, sb.greloc, sb.bkeys};
+    for (void *p : ps) if (p) cudaFree(p);
+    sb = StageBufs();
+    CKC(cudaMalloc((void **)&sb.cu, 4 * c)); CKC(cudaMalloc((void **)&sb.cv, 4 * c));
+    CKC(cudaMalloc((void **)&sb.cop, c));
+    CKC(cudaMalloc((void **)&sb.keys, 16 * c)); CKC(cudaMalloc((void **)&sb.tk, 16 * c));
+    CKC(cudaMalloc((void **)&sb.vals, 8 * c)); CKC(cudaMalloc((void **)&sb.tv, 8 * c));
+    CKC(cudaMalloc((void **)&sb.head, 8 * c)); CKC(cudaMalloc((void **)&sb.gid, 8 * c));
+    CKC(cudaMalloc((void **)&sb.gv, 8 * c)); CKC(cudaMalloc((void **)&sb.gstart, 8 * c));
+    CKC(cudaMalloc((void **)&sb.gins, 8 * c)); CKC(cudaMalloc((void **)&sb.greloc, 8 * c));
+    CKC(cudaMalloc((void **)&sb.bkeys, 8 * c));
+    sb.cap = c;
+  }
+  const int8_t *dop = op;
+  const int32_t *dsrc = src, *ddst = dst;
+  if (b > 0) {
+    bool dev = is_device_ptr(op) && is_device_ptr(src) && is_device_ptr(dst);
+    if (!dev) {
+      if (b > ctx->in_cap) {
+        cudaFree(ctx->d_in_op); cudaFree(ctx->d_in_src); cudaFree(ctx->d_in_dst);
+        ctx->d_in_op = nullptr; ctx->d_in_src = nullptr; ctx->d_in_dst = nullptr;
+        int64_t c = std::max<int64_t>(b, 1024);
+        CKC(cudaMalloc((void **)&ctx->d_in_op, c));
+        CKC(cudaMalloc((void **)&ctx->d_in_src, 4 * c));
+        CKC(cudaMalloc((void **)&ctx->d_in_dst, 4 * c));
+        ctx->in_cap = c;
+      }
+      CKC(cudaMemcpyAsync(ctx->d_in_op, op, b, cudaMemcpyDefault, s));
+      CKC(cudaMemcpyAsync(ctx->d_in_src, src, 4 * b, cudaMemcpyDefault, s));
+      CKC(cudaMemcpyAsync(ctx->d_in_dst, dst, 4 * b, cudaMemcpyDefault, s));
+      dop = ctx->d_in_op; dsrc = ctx->d_in_src; ddst = ctx->d_in_dst;
+    }
+  }
+  for (int attempt = 0; attempt < 3; attempt++) {
+    reset_status_host(ctx);
+    CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
+    CKC(cudaEventRecord(ctx->ev[0], s));
+    if (b > 0) CK(gm_stage(ctx->gd(), dop, dsrc, ddst, b, sb, ctx->d_st, s));
+    CKC(cudaEventRecord(ctx->ev[1], s));
+    CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
+    CKC(cudaStreamSynchronize(s));
+    if (ctx->h_st->err == GAMMA_ENOMEM) {
+      CK(grow_pool(ctx, ctx->pool_top + ctx->h_st->reloc_total));
+      continue;
+    }
+    break;
+  }
+  GmStatus st0 = *ctx->h_st;
+  if (st0.err == GAMMA_EINVAL) {
+    if (st0.bad_index != INT64_MAX)
+      return ctx->fail(GAMMA_EINVAL,
+                       "gamma_apply_batch: update %lld is invalid (bad op or id, self-loop, repeated edge, "
+                       "insertion of an existing edge or deletion of a missing one); graph unchanged",
+                       (long long)st0.bad_index);
+    return ctx->fail(GAMMA_EINVAL, "gamma_apply_batch: invalid batch; graph unchanged");
+  }
+  if (st0.err) return ctx->fail(st0.err, "gamma_apply_batch: staging failed (code %d)", st0.err);
+  ctx->stats.ms_stage = ev_ms(ctx->ev[0], ctx->ev[1]);
+  ctx->pool_top = st0.pool_top;
+  ctx->stats.touched = st0.ntouched;
+  ctx->b = b;
+  ctx->staged = true;
+  ctx->qids.assign(qids, qids + nq);
+  int rc = match_with_rows(ctx, opt_out);
+  if (rc != GAMMA_OK && rc != GAMMA_EOVERFLOW) return ctx->err.empty() ? ctx->fail(rc, "match failed") : rc;
+  for (int j = 0; j < nq; j++) {
+    out_pos[j] = ctx->h_cnt[2 * j];
+    out_neg[j] = ctx->h_cnt[2 * j + 1];
+  }
+  ctx->stats.pool_used = (int64_t)ctx->pool_top;
+  ctx->stats.pool_cap = ctx->pool_cap;
+  if (ctx->h_st->err == GAMMA_ETIMEOUT)
+    return ctx->fail(GAMMA_ETIMEOUT, "gamma_apply_batch: work budget exceeded; counts are incomplete");
+  if (ctx->h_st->err) return ctx->fail(ctx->h_st->err, "gamma_apply_batch: matching failed (code %d)", ctx->h_st->err);
+  if (rc == GAMMA_EOVERFLOW)
+    return ctx->fail(GAMMA_EOVERFLOW, "gamma_apply_batch: %lld match rows do not fit in %lld",
+                     (long long)opt_out->required, (long long)opt_out->capacity);
+  return GAMMA_OK;
+}
+
+int gamma_fetch_matches(gamma_ctx *ctx, gamma_matches *out) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->staged) return ctx->fail(GAMMA_ESTATE, "gamma_fetch_matches: no staged batch");
+  if (!out) return ctx->fail(GAMMA_EINVAL, "gamma_fetch_matches: null output");
+  cudaSetDevice(ctx->device);
+  int rc = match_with_rows(ctx, out);
+  if (rc != GAMMA_OK && rc != GAMMA_EOVERFLOW) return rc;
+  if (ctx->h_st->err) return ctx->fail(ctx->h_st->err, "gamma_fetch_matches: matching failed (code %d)", ctx->h_st->err);
+  if (rc == GAMMA_EOVERFLOW)
+    return ctx->fail(GAMMA_EOVERFLOW, "gamma_fetch_matches: %lld rows do not fit in %lld",
+                     (long long)out->required, (long long)out->capacity);
+  return GAMMA_OK;
+}
+
+int gamma_update_counts(gamma_ctx *ctx, int32_t j, uint64_t *out) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->staged) return ctx->fail(GAMMA_ESTATE, "gamma_update_counts: no staged batch");
+  if (!(ctx->flags & GAMMA_F_PER_UPDATE)) return ctx->fail(GAMMA_ESTATE, "gamma_update_counts: GAMMA_F_PER_UPDATE not set");
+  if (j < 0 || j >= (int)ctx->qids.size() || !out) return ctx->fail(GAMMA_EINVAL, "gamma_update_counts: bad query slot");
+  if (ctx->b == 0) return GAMMA_OK;
+  cudaSetDevice(ctx->device);
+  CKC(cudaMemcpy(out, ctx->d_per_upd + (size_t)j * ctx->b, sizeof(uint64_t) * ctx->b, cudaMemcpyDeviceToHost));
+  return GAMMA_OK;
+}
+
+int gamma_commit(gamma_ctx *ctx) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->staged) return ctx->fail(GAMMA_ESTATE, "gamma_commit: no staged batch");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  CKC(cudaMemsetAsync(&ctx->d_st->live, 0, sizeof(uint64_t), s));
+  CKC(cudaEventRecord(ctx->ev[6], s));
+  if (ctx->b > 0) CK(gm_commit(ctx->gd(), ctx->sb, ctx->b, ctx->d_st, s));
+  CKC(cudaEventRecord(ctx->ev[7], s));
+  CKC(cudaMemcpyAsync(&ctx->h_st->live, &ctx->d_st->live, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  CKC(cudaStreamSynchronize(s));
+  ctx->live += (int64_t)ctx->h_st->live;  // signed change, two's complement
+  ctx->stats.ms_commit = ev_ms(ctx->ev[6], ctx->ev[7]);
+  ctx->staged = false;
+  return GAMMA_OK;
+}
+
+int gamma_export_adjacency(gamma_ctx *ctx, int64_t *off, int32_t *nbr, int32_t *tag, int64_t cap) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "gamma_export_adjacency: no graph loaded");
+  if (!off || (cap > 0 && (!nbr || !tag))) return ctx->fail(GAMMA_EINVAL, "gamma_export_adjacency: null arrays");
+  cudaSetDevice(ctx->device);
+  CKC(cudaStreamSynchronize(ctx->stream));
+  std::vector<uint2> adj(ctx->n);
+  std::vector<uint32_t> col(ctx->pool_top), etag(ctx->pool_top);
+  CKC(cudaMemcpy(adj.data(), ctx->d_adj, sizeof(uint2) * ctx->n, cudaMemcpyDeviceToHost));
+  if (ctx->pool_top) {
+    CKC(cudaMemcpy(col.data(), ctx->d_col, sizeof(uint32_t) * ctx->pool_top, cudaMemcpyDeviceToHost));
+    CKC(cudaMemcpy(etag.data(), ctx->d_etag, sizeof(uint32_t) * ctx->pool_top, cudaMemcpyDeviceToHost));
+  }
+  const uint32_t idmask = ctx->gd().idmask;
+  int64_t k = 0;
+  off[0] = 0;
+  for (int32_t v = 0; v < ctx->n; v++) {
+    for (uint32_t i = 0; i < adj[v].y; i++, k++) {
+      if (k < cap) {
+        uint32_t x = col[adj[v].x + i];
+        nbr[k] = (int32_t)((x >> 1) & idmask);
+        tag[k] = (x & 1u) ? (int32_t)etag[adj[v].x + i] : -1;
+      }
+    }
+    off[v + 1] = k;
+  }
+  return k > cap ? ctx->fail(GAMMA_EOVERFLOW, "gamma_export_adjacency: %lld entries > cap", (long long)k) : GAMMA_OK;
+}
+
+int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out) {
+  if (!ctx || !out) return GAMMA_EINVAL;
+  *out = ctx->stats;
+  out->pool_used = (int64_t)ctx->pool_top;
+  out->pool_cap = ctx->pool_cap;
+  out->live_edges = ctx->live;
+  return GAMMA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// gm_graph.cuh -- host entry points of the dynamic-CSR kernels (gm_graph.cu)
+// and the match kernels (gm_match.cu).
+#pragma once
+#include "gm_common.cuh"
+
+// per-batch device buffers (sized for 2b directed entries)
+struct StageBufs {
+  uint32_t *cu = nullptr, *cv = nullptr;  // canonical endpoints (min, max) per update
+  int8_t *cop = nullptr;                  // op per update
+  uint64_t *keys = nullptr, *tk = nullptr;
+  uint32_t *vals = nullptr, *tv = nullptr;
+  uint32_t *head = nullptr, *gid = nullptr;
+  uint32_t *gv = nullptr, *gstart = nullptr, *gins = nullptr, *greloc = nullptr;
+  uint32_t *bkeys = nullptr;
+  int64_t cap = 0;  // updates
+};
+
+int gm_load_validate(const int32_t *labels, int32_t n, const int32_t *src, const int32_t *dst, int64_t m,
+                     GmStatus *st, cudaStream_t s);
+int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m, uint32_t **col_out,
+                  uint32_t **etag_out, uint32_t *pool_cap_out, double pool_factor, uint64_t pool_reserve,
+                  GmStatus *st, GmStatus *h_st, cudaStream_t s);
+int gm_nlf(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32_t nverts_max, cudaStream_t s);
+int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, int64_t b, StageBufs &sb,
+             GmStatus *st, cudaStream_t s);
+int gm_commit(GraphDev g, const StageBufs &sb, int64_t b, GmStatus *st, cudaStream_t s);
+// per-query form: the next DFS launch starts at the items the next seed launch appends
+int gm_begin_group(GmStatus *st, cudaStream_t s);
+
+// ---------------------------------------------------------------- matching
+struct MatchArgs {
+  GraphDev g;
+  const uint32_t *cu, *cv;     // canonical endpoints per update
+  const int8_t *op;
+  int64_t b;
+  const Plan *plans;
+  int nplans;
+  const uint32_t *pair_off;    // [nlab*nlab + 1] plans per (L(min), L(max)) label pair
+  const uint16_t *pair_plans;
+  int grain;                   // level-2 candidates per work item
+  WorkItem *items;
+  uint64_t item_cap;
+  uint64_t *cnt;               // [nq * 2] positive / negative counts
+  uint64_t *per_upd;           // [nq * b] or null
+  int use_filter;
+  int32_t *rows;               // match rows or null
+  uint64_t row_cap;
+  int row_stride;
+  uint64_t budget;
+  int tile;                    // DFS frontier tile
+  int nlev;                    // stored DFS levels (max q - 3, >= 1)
+  int warps_per_block;
+  GmStatus *st;
+};
+
+int gm_seed(const MatchArgs &a, cudaStream_t s);
+int gm_dfs(const MatchArgs &a, int num_sms, cudaStream_t s);
+size_t gm_dfs_smem_per_warp(int tile, int nlev);

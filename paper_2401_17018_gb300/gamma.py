@@ -1,0 +1,296 @@
+"""Python binding of libgamma (include/gamma.h): argument marshalling only.
+
+The module-level functions carry the C-ABI names and take plain arrays:
+numpy arrays (host) or torch tensors (host or CUDA); the library decides
+where each pointer lives. Every step of the matching runs in the CUDA
+library; if ``_build/libgamma.so`` cannot be loaded, importing the binding
+raises instead of falling back to anything else. ``Context`` wraps the same
+calls for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+GAMMA_OK, GAMMA_EINVAL, GAMMA_ENOMEM, GAMMA_ESTATE, GAMMA_EOVERFLOW, GAMMA_ETIMEOUT, GAMMA_ECUDA = (
+    0, -1, -2, -3, -4, -5, -6)
+GAMMA_F_PER_UPDATE, GAMMA_F_NO_FILTER, GAMMA_F_PER_QUERY, GAMMA_F_GRAPH = 0x1, 0x2, 0x4, 0x8
+
+_NAMES = {0: "GAMMA_OK", -1: "GAMMA_EINVAL", -2: "GAMMA_ENOMEM", -3: "GAMMA_ESTATE",
+          -4: "GAMMA_EOVERFLOW", -5: "GAMMA_ETIMEOUT", -6: "GAMMA_ECUDA"}
+
+
+class gamma_options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("flags", ctypes.c_uint32),
+                ("work_budget", ctypes.c_uint64), ("warps_per_block", ctypes.c_int),
+                ("frontier_tile", ctypes.c_int), ("steal_grain", ctypes.c_int)]
+
+
+class gamma_matches(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_void_p), ("capacity", ctypes.c_int64), ("stride", ctypes.c_int32),
+                ("written", ctypes.c_int64), ("required", ctypes.c_int64)]
+
+
+class gamma_stats(ctypes.Structure):
+    _fields_ = [("ms_stage", ctypes.c_double), ("ms_seed", ctypes.c_double), ("ms_match", ctypes.c_double),
+                ("ms_finalize", ctypes.c_double), ("ms_commit", ctypes.c_double), ("seeds", ctypes.c_int64),
+                ("work_items", ctypes.c_int64), ("touched", ctypes.c_int64), ("pool_used", ctypes.c_int64),
+                ("pool_cap", ctypes.c_int64), ("live_edges", ctypes.c_int64), ("expansions", ctypes.c_uint64)]
+
+
+class GammaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "gamma_create": (ctypes.c_int, [ctypes.POINTER(gamma_options), ctypes.POINTER(ctypes.c_void_p)]),
+    "gamma_destroy": (None, [_P]),
+    "gamma_load_graph": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P]),
+    "gamma_register_query": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "gamma_apply_batch": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int32, _P, _P, _P,
+                                         ctypes.POINTER(gamma_matches)]),
+    "gamma_fetch_matches": (ctypes.c_int, [_P, ctypes.POINTER(gamma_matches)]),
+    "gamma_update_counts": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "gamma_commit": (ctypes.c_int, [_P]),
+    "gamma_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(gamma_stats)]),
+    "gamma_export_adjacency": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
+    "gamma_set_options": (ctypes.c_int, [_P, ctypes.POINTER(gamma_options)]),
+    "gamma_last_error": (ctypes.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libgamma.so (building it first if needed); raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError("libgamma.so is not built (%s); run paper_2401_17018_gb300.build" % _build.LIB)
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a numpy array or torch tensor (contiguous), or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError("expected a numpy array or a torch tensor, got %r" % type(a))
+
+
+def _as(a, dtype):
+    if hasattr(a, "data_ptr"):
+        import torch
+        want = {np.int8: torch.int8, np.int32: torch.int32}[dtype]
+        return a.to(want).contiguous()
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _check(ctx, rc: int):
+    if rc != GAMMA_OK:
+        msg = load_library().gamma_last_error(ctx) if ctx else b""
+        raise GammaError(rc, (msg or b"").decode())
+
+
+# ----------------------------------------------------------- C-ABI names
+def gamma_create(options: Optional[gamma_options] = None) -> int:
+    lib = load_library()
+    out = ctypes.c_void_p()
+    rc = lib.gamma_create(ctypes.byref(options) if options is not None else None, ctypes.byref(out))
+    if rc != GAMMA_OK:
+        raise GammaError(rc, "gamma_create failed")
+    return out.value
+
+
+def gamma_destroy(ctx: int) -> None:
+    load_library().gamma_destroy(ctx)
+
+
+def gamma_load_graph(ctx: int, n: int, labels, src, dst) -> None:
+    labels, src, dst = _as(labels, np.int32), _as(src, np.int32), _as(dst, np.int32)
+    _check(ctx, load_library().gamma_load_graph(ctx, int(n), _ptr(labels), int(src.shape[0]), _ptr(src), _ptr(dst)))
+
+
+def gamma_register_query(ctx: int, labels, src, dst) -> int:
+    labels, src, dst = _as(labels, np.int32), _as(src, np.int32), _as(dst, np.int32)
+    qid = ctypes.c_int32(-1)
+    _check(ctx, load_library().gamma_register_query(ctx, int(labels.shape[0]), _ptr(labels), int(src.shape[0]),
+                                                    _ptr(src), _ptr(dst), ctypes.byref(qid)))
+    return qid.value
+
+
+def gamma_apply_batch(ctx: int, op, src, dst, qids: Sequence[int], matches: Optional[gamma_matches] = None
+                      ) -> Tuple[np.ndarray, np.ndarray, int]:
+    """Returns (pos counts, neg counts, rc); rc is GAMMA_OK or GAMMA_EOVERFLOW
+    (other codes raise)."""
+    op, src, dst = _as(op, np.int8), _as(src, np.int32), _as(dst, np.int32)
+    q = np.ascontiguousarray(qids, dtype=np.int32)
+    pos = np.zeros(max(q.size, 1), np.uint64)
+    neg = np.zeros(max(q.size, 1), np.uint64)
+    rc = load_library().gamma_apply_batch(ctx, int(op.shape[0]), _ptr(op), _ptr(src), _ptr(dst), int(q.size),
+                                          _ptr(q), _ptr(pos), _ptr(neg),
+                                          ctypes.byref(matches) if matches is not None else None)
+    if rc not in (GAMMA_OK, GAMMA_EOVERFLOW):
+        _check(ctx, rc)
+    return pos[:q.size], neg[:q.size], rc
+
+
+def gamma_fetch_matches(ctx: int, matches: gamma_matches) -> int:
+    rc = load_library().gamma_fetch_matches(ctx, ctypes.byref(matches))
+    if rc not in (GAMMA_OK, GAMMA_EOVERFLOW):
+        _check(ctx, rc)
+    return rc
+
+
+def gamma_update_counts(ctx: int, j: int, b: int) -> np.ndarray:
+    out = np.zeros(max(b, 1), np.uint64)
+    _check(ctx, load_library().gamma_update_counts(ctx, int(j), _ptr(out)))
+    return out[:b]
+
+
+def gamma_commit(ctx: int) -> None:
+    _check(ctx, load_library().gamma_commit(ctx))
+
+
+def gamma_get_stats(ctx: int) -> dict:
+    st = gamma_stats()
+    _check(ctx, load_library().gamma_get_stats(ctx, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in gamma_stats._fields_}
+
+
+def gamma_export_adjacency(ctx: int, n: int, cap: int):
+    """(off[n+1], nbr, tag) of the current (union) adjacency."""
+    off = np.zeros(n + 1, np.int64)
+    nbr = np.zeros(max(cap, 1), np.int32)
+    tag = np.zeros(max(cap, 1), np.int32)
+    _check(ctx, load_library().gamma_export_adjacency(ctx, _ptr(off), _ptr(nbr), _ptr(tag), int(cap)))
+    return off, nbr[:off[-1]], tag[:off[-1]]
+
+
+def gamma_set_options(ctx: int, options: gamma_options) -> None:
+    _check(ctx, load_library().gamma_set_options(ctx, ctypes.byref(options)))
+
+
+def gamma_last_error(ctx: int) -> str:
+    return (load_library().gamma_last_error(ctx) or b"").decode()
+
+
+# ----------------------------------------------------------- convenience
+def make_options(device: int = 0, stream=None, flags: int = 0, work_budget: int = 0, warps_per_block: int = 0,
+                 frontier_tile: int = 0, steal_grain: int = 0) -> gamma_options:
+    s = stream
+    if s is not None and hasattr(s, "cuda_stream"):
+        s = s.cuda_stream
+    return gamma_options(device, s, flags, work_budget, warps_per_block, frontier_tile, steal_grain)
+
+
+class Context:
+    """One libgamma context (see include/gamma.h for the state machine)."""
+
+    def __init__(self, device: int = 0, stream=None, flags: int = 0, work_budget: int = 0,
+                 warps_per_block: int = 0, frontier_tile: int = 0, steal_grain: int = 0):
+        self._opts = make_options(device, stream, flags, work_budget, warps_per_block, frontier_tile, steal_grain)
+        self.h = gamma_create(self._opts)
+        self.b = 0
+        self.qsizes = {}
+
+    def close(self):
+        if self.h:
+            gamma_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            if k == "stream" and v is not None and hasattr(v, "cuda_stream"):
+                v = v.cuda_stream
+            setattr(self._opts, "cuda_stream" if k == "stream" else k, v)
+        gamma_set_options(self.h, self._opts)
+
+    def load_graph(self, n, labels, src, dst):
+        gamma_load_graph(self.h, n, labels, src, dst)
+        self.qsizes = {}
+
+    def register_query(self, labels, src, dst) -> int:
+        qid = gamma_register_query(self.h, labels, src, dst)
+        self.qsizes[qid] = int(len(labels))
+        return qid
+
+    def apply_batch(self, op, src, dst, qids: Sequence[int], row_capacity: Optional[int] = None,
+                    rows=None):
+        """Apply a batch. With row_capacity (host rows) or rows (a preallocated
+        int32 buffer, host or device, shape [capacity, stride]) the match rows
+        are returned too: (pos, neg, rows_written, required)."""
+        self.b = int(op.shape[0])
+        m = None
+        buf = None
+        if rows is not None or row_capacity is not None:
+            stride = 3 + max([self.qsizes.get(int(q), 2) for q in qids] + [2])
+            if rows is None:
+                buf = np.full((max(int(row_capacity), 1), stride), -1, np.int32)
+            else:
+                buf = rows
+                stride = int(buf.shape[1])
+            m = gamma_matches(_ptr(buf), int(buf.shape[0]) if row_capacity is None else int(row_capacity), stride, 0, 0)
+        pos, neg, rc = gamma_apply_batch(self.h, op, src, dst, qids, m)
+        if m is None:
+            return pos, neg
+        return pos, neg, buf[:m.written], m.required
+
+    def fetch_matches(self, rows):
+        m = gamma_matches(_ptr(rows), int(rows.shape[0]), int(rows.shape[1]), 0, 0)
+        gamma_fetch_matches(self.h, m)
+        return rows[:m.written], m.required
+
+    def update_counts(self, j: int) -> np.ndarray:
+        return gamma_update_counts(self.h, j, self.b)
+
+    def commit(self):
+        gamma_commit(self.h)
+
+    def stats(self) -> dict:
+        return gamma_get_stats(self.h)
+
+    def export_adjacency(self, n: int):
+        st = self.stats()
+        return gamma_export_adjacency(self.h, n, int(st["pool_used"]))

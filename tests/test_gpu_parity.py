@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Counts, per-update charges and sorted match rows must agree bit for bit
+(everything on the path is integer).  Inputs are seeded and synthetic.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2401_17018_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2401_17018_gb300 import gamma
+    return gamma
+
+
+def gpu_run(G, graph, queries, batch, flags=0, rows=True, **opts):
+    """Apply one batch on a fresh context; returns counts, per-update counts, rows."""
+    with G.Context(flags=flags | G.GAMMA_F_PER_UPDATE, **opts) as ctx:
+        ctx.load_graph(graph.n, graph.labels, graph.src, graph.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
+        if rows:
+            pos, neg, r, req = ctx.apply_batch(batch.op, batch.src, batch.dst, qids, row_capacity=1 << 20)
+            assert req == len(r)
+        else:
+            pos, neg = ctx.apply_batch(batch.op, batch.src, batch.dst, qids)
+            r = None
+        per = [ctx.update_counts(j) for j in range(len(qids))]
+        st = ctx.stats()
+        ctx.commit()
+    return pos, neg, per, r, st
+
+
+def oracle_run(graph, q, batch, rows=True):
+    c, t = O.bdsm(graph.n, graph.labels, graph.src, graph.dst, q, batch, want_tuples=rows)
+    return c, t
+
+
+def rowset(r, qid):
+    return sorted((int(x[1]), int(x[2])) + tuple(int(v) for v in x[3:]) for x in r if x[0] == qid)
+
+
+def orowset(t, q):
+    return sorted((int(x[0]), int(x[1])) + tuple(int(v) for v in x[2:]) for x in t)
+
+
+def check(G, graph, queries, batch, rows=True, flags=0, **opts):
+    pos, neg, per, r, st = gpu_run(G, graph, queries, batch, flags=flags, rows=rows, **opts)
+    for j, q in enumerate(queries):
+        c, t = oracle_run(graph, q, batch, rows)
+        assert (int(pos[j]), int(neg[j])) == O.totals(c, batch.op), f"query {j}"
+        assert np.array_equal(per[j], c), f"per-update counts, query {j}"
+        if rows:
+            got = [x[:2 + q.q] for x in rowset(r, j)]
+            assert got == orowset(t, q), f"rows, query {j}"
+    return pos, neg, st
+
+
+def _golden_running():
+    with open(os.path.join(GOLD, "running_example.json")) as f:
+        d = json.load(f)
+    e = np.array(d["edges"], np.int32)
+    g = I.Graph(d["n"], np.array(d["labels"], np.int32), e[:, 0].copy(), e[:, 1].copy())
+    q = I.pattern_query(d["query"]["labels"], [tuple(x) for x in d["query"]["edges"]])
+    b = I.Batch(np.array(d["batch"]["op"], np.int8), np.array(d["batch"]["src"], np.int32),
+                np.array(d["batch"]["dst"], np.int32))
+    return d, g, q, b
+
+
+def test_running_example(G):
+    d, g, q, b = _golden_running()
+    pos, neg, _ = check(G, g, [q], b)
+    assert (int(pos[0]), int(neg[0])) == (d["bdsm"]["pos"], d["bdsm"]["neg"])
+
+
+def test_running_example_csm_sequence(G):
+    d, g, q, b = _golden_running()
+    with G.Context() as ctx:
+        ctx.load_graph(g.n, g.labels, g.src, g.dst)
+        qid = ctx.register_query(q.labels, q.src, q.dst)
+        got = []
+        for k in range(len(b)):
+            pos, neg = ctx.apply_batch(b.op[k:k + 1], b.src[k:k + 1], b.dst[k:k + 1], [qid])
+            got.append((int(pos[0]), int(neg[0])))
+            ctx.commit()
+    assert got == [(c["pos"], c["neg"]) for c in d["csm"]]
+
+
+def test_tiny_workload(G):
+    w = I.make_workload("tiny")
+    b = I.workload_batch(w, 256, 0)
+    check(G, w.graph, [I.TRIANGLE_WITH_TAIL], b)
+
+
+def test_tiny_workload_mixed_many_queries(G):
+    w = I.make_workload("tiny")
+    g = w.graph
+    b = I.workload_batch(w, 600, 300, sub=1)
+    off, nbr = I.csr_from_edges(g.n, g.src, g.dst)
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1], [(0, 1)]), I.pattern_query([2, 2], [(0, 1)]),
+          I.pattern_query([1, 2, 3], [(0, 1), (1, 2)])]
+    att = 0
+    while len(qs) < 12:
+        kind = ["dense", "sparse", "tree"][att % 3]
+        q = I.random_walk_query(off, nbr, g.labels, 4 + att % 3, kind, 5, att)
+        att += 1
+        if q is not None:
+            qs.append(q)
+    check(G, g, qs, b)
+
+
+@pytest.mark.parametrize("trial", range(40))
+def test_fuzz_small_graphs(G, trial):
+    r = np.random.default_rng(1000 + trial)
+    n = int(r.integers(6, 40))
+    g = I.random_small_graph(n, int(r.integers(10, 60)), int(r.integers(1, 4)), 9, trial)
+    es = set(zip(g.src.tolist(), g.dst.tolist()))
+    non = [(a, b) for a in range(n) for b in range(a + 1, n) if (a, b) not in es]
+    el = sorted(es)
+    ni = min(len(non), int(r.integers(0, 20)))
+    nd = min(len(el), int(r.integers(0, 10)))
+    ins = [non[i] for i in r.choice(len(non), ni, replace=False)] if ni else []
+    dl = [el[i] for i in r.choice(len(el), nd, replace=False)] if nd else []
+    ed = ins + dl
+    ops = [1] * ni + [-1] * nd
+    perm = r.permutation(len(ed))
+    if len(ed) == 0:
+        pytest.skip("empty batch")
+    b = I.Batch(np.array([ops[i] for i in perm], np.int8), np.array([ed[i][1] for i in perm], np.int32),
+                np.array([ed[i][0] for i in perm], np.int32))
+    nl = int(g.labels.max()) + 1
+    qs = []
+    for k in range(5):
+        q = int(r.integers(2, 6))
+        edges = [(i, int(r.integers(0, i))) for i in range(1, q)]
+        for _ in range(int(r.integers(0, 3))):
+            a, c = sorted(r.choice(q, 2, replace=False).tolist())
+            if (a, c) not in edges and (c, a) not in edges:
+                edges.append((a, c))
+        qs.append(I.pattern_query(r.integers(0, nl, q).tolist(), edges))
+    flags = [0, 2, 4][trial % 3]
+    check(G, g, qs, b, flags=flags, frontier_tile=[32, 64, 128][trial % 3], steal_grain=[1, 3, 64][trial % 3])
+
+
+def test_empty_batch_and_no_queries(G):
+    w = I.make_workload("tiny")
+    with G.Context() as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qid = ctx.register_query(I.TRIANGLE_WITH_TAIL.labels, I.TRIANGLE_WITH_TAIL.src, I.TRIANGLE_WITH_TAIL.dst)
+        e = np.zeros(0, np.int32)
+        pos, neg = ctx.apply_batch(np.zeros(0, np.int8), e, e, [qid])
+        assert (int(pos[0]), int(neg[0])) == (0, 0)
+        ctx.commit()
+        b = I.workload_batch(w, 10, 0)
+        pos, neg = ctx.apply_batch(b.op, b.src, b.dst, [])
+        assert len(pos) == 0
+        ctx.commit()
+
+
+@pytest.mark.parametrize("case,bad", [
+    ("dup_same", 3), ("insert_existing", 2), ("delete_missing", 1), ("self_loop", 0), ("bad_id", 2),
+    ("ins_del_same_edge", 2), ("bad_op", 1)])
+def test_invalid_batch_rejected_and_graph_unchanged(G, case, bad):
+    g = I.Graph(6, np.zeros(6, np.int32), np.array([0, 1, 2], np.int32), np.array([1, 2, 3], np.int32))
+    ops, src, dst = {
+        "dup_same": ([1, 1, 1, 1], [0, 4, 0, 5], [4, 5, 5, 4]),
+        "insert_existing": ([1, -1, 1], [0, 0, 2], [4, 1, 1]),
+        "delete_missing": ([1, -1, 1], [0, 0, 3], [4, 5, 5]),
+        "self_loop": ([1, 1], [2, 0], [2, 4]),
+        "bad_id": ([1, 1, 1], [0, 1, 9], [4, 4, 0]),
+        "ins_del_same_edge": ([1, 1, -1], [0, 1, 4], [4, 5, 0]),
+        "bad_op": ([1, 2, 1], [0, 1, 2], [4, 4, 4]),
+    }[case]
+    q = I.pattern_query([0, 0, 0], [(0, 1), (1, 2)])
+    good = I.Batch(np.array([1, -1], np.int8), np.array([3, 1], np.int32), np.array([4, 2], np.int32))
+    c_ref, _ = O.bdsm(g.n, g.labels, g.src, g.dst, q, good)
+    with G.Context() as ctx:
+        ctx.load_graph(g.n, g.labels, g.src, g.dst)
+        qid = ctx.register_query(q.labels, q.src, q.dst)
+        with pytest.raises(G.GammaError) as e:
+            ctx.apply_batch(np.array(ops, np.int8), np.array(src, np.int32), np.array(dst, np.int32), [qid])
+        assert e.value.code == G.GAMMA_EINVAL
+        assert ("update %d " % bad) in str(e.value)
+        pos, neg = ctx.apply_batch(good.op, good.src, good.dst, [qid])
+        assert (int(pos[0]), int(neg[0])) == O.totals(c_ref, good.op)
+
+
+def test_state_machine(G):
+    with G.Context() as ctx:
+        with pytest.raises(G.GammaError) as e:
+            ctx.commit()
+        assert e.value.code == G.GAMMA_ESTATE
+        g = I.Graph(4, np.zeros(4, np.int32), np.array([0], np.int32), np.array([1], np.int32))
+        ctx.load_graph(g.n, g.labels, g.src, g.dst)
+        qid = ctx.register_query([0, 0], [0], [1])
+        b = I.Batch(np.array([1], np.int8), np.array([2], np.int32), np.array([3], np.int32))
+        ctx.apply_batch(b.op, b.src, b.dst, [qid])
+        with pytest.raises(G.GammaError) as e:
+            ctx.apply_batch(b.op, b.src, b.dst, [qid])
+        assert e.value.code == G.GAMMA_ESTATE
+        ctx.commit()
+        with pytest.raises(G.GammaError):
+            ctx.register_query([0, 0, 0], [0], [1])  # disconnected
+
+
+def test_sequence_of_batches_with_commit(G):
+    """Five consecutive mixed batches on a scaled-down large-workload graph."""
+    w = I.make_workload("large", scale=14, n_edges=120_000)
+    g = w.graph
+    cs, cd = g.src, g.dst
+    off, nbr = I.csr_from_edges(g.n, g.src, g.dst)
+    qs = []
+    att = 0
+    while len(qs) < 4:
+        q = I.random_walk_query(off, nbr, g.labels, 5, ["dense", "sparse"][att % 2], 3, att)
+        att += 1
+        if q is not None:
+            qs.append(q)
+    with G.Context(flags=G.GAMMA_F_PER_UPDATE) as ctx:
+        ctx.load_graph(g.n, g.labels, g.src, g.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        start = 0
+        for it in range(5):
+            b = I.workload_batch(w, 1600, 400, sub=it, pool_start=start, cur=(cs, cd))
+            start += 1600
+            pos, neg = ctx.apply_batch(b.op, b.src, b.dst, qids)
+            for j, q in enumerate(qs):
+                c, _ = O.bdsm(g.n, g.labels, cs, cd, q, b)
+                assert (int(pos[j]), int(neg[j])) == O.totals(c, b.op), (it, j)
+                assert np.array_equal(ctx.update_counts(j), c)
+            ctx.commit()
+            cs, cd = I.apply_batch_edges(cs, cd, b)
+        st = ctx.stats()
+        assert st["live_edges"] == 2 * cs.size
+
+
+def test_options_do_not_change_results(G):
+    w = I.make_workload("tiny")
+    b = I.workload_batch(w, 500, 200, sub=3)
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 0, 1, 1], [(0, 1), (1, 2), (2, 3), (3, 0)])]
+    ref = None
+    for flags, tile, grain, wpb in [(0, 64, 64, 8), (2, 32, 1, 4), (4, 128, 7, 16), (6, 256, 1024, 2)]:
+        pos, neg, _, _, _ = gpu_run(G, w.graph, qs, b, flags=flags, rows=False, frontier_tile=tile,
+                                    steal_grain=grain, warps_per_block=wpb)
+        got = (pos.tolist(), neg.tolist())
+        if ref is None:
+            ref = got
+        assert got == ref
+
+
+def test_row_overflow_and_fetch(G):
+    w = I.make_workload("tiny")
+    b = I.workload_batch(w, 256, 0)
+    q = I.TRIANGLE_WITH_TAIL
+    c, t = oracle_run(w.graph, q, b)
+    total = int(c.sum())
+    assert total > 4
+    with G.Context() as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qid = ctx.register_query(q.labels, q.src, q.dst)
+        pos, neg, r, req = ctx.apply_batch(b.op, b.src, b.dst, [qid], row_capacity=3)
+        assert int(pos[0]) + int(neg[0]) == total and req == total and len(r) == 3
+        big = np.full((total, 3 + q.q), -1, np.int32)
+        r2, req2 = ctx.fetch_matches(big)
+        assert req2 == total
+        assert [x[:2 + q.q] for x in rowset(r2, qid)] == orowset(t, q)
+        ctx.commit()
+
+
+def test_device_pointer_inputs(G):
+    import torch
+    w = I.make_workload("tiny")
+    b = I.workload_batch(w, 256, 50, sub=2)
+    q = I.TRIANGLE_WITH_TAIL
+    c, _ = oracle_run(w.graph, q, b, rows=False)
+    with G.Context(stream=torch.cuda.current_stream()) as ctx:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        ctx.load_graph(w.graph.n, dev(w.graph.labels), dev(w.graph.src), dev(w.graph.dst))
+        qid = ctx.register_query(q.labels, q.src, q.dst)
+        pos, neg = ctx.apply_batch(dev(b.op), dev(b.src), dev(b.dst), [qid])
+        assert (int(pos[0]), int(neg[0])) == O.totals(c, b.op)
+        ctx.commit()
+
+
+def test_work_budget_times_out_cleanly(G):
+    w = I.make_workload("tiny")
+    b = I.workload_batch(w, 256, 0)
+    with G.Context(work_budget=1) as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qid = ctx.register_query(I.TRIANGLE_WITH_TAIL.labels, I.TRIANGLE_WITH_TAIL.src, I.TRIANGLE_WITH_TAIL.dst)
+        with pytest.raises(G.GammaError) as e:
+            ctx.apply_batch(b.op, b.src, b.dst, [qid])
+        assert e.value.code == G.GAMMA_ETIMEOUT
+        ctx.commit()  # the graph is staged and still consistent
+        ctx.set_options(work_budget=0)
+        b2 = I.workload_batch(w, 10, 0, pool_start=300)
+        ctx.apply_batch(b2.op, b2.src, b2.dst, [qid])
+        ctx.commit()
