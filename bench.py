@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Benchmark of batch-dynamic subgraph matching (BDSM) on GB300.
+
+One step = one pass of the whole hot path over one update batch: stage the
+batch into the device-resident dynamic CSR (A1), seed (A2), DFS extension
+(A5) with match counting (A6), counts back to the host, commit (A8).
+Steps alternate the batch and its inverse, so the graph cycles between G0
+and G0 + batch and every step does the same amount of work.
+
+Default workload ("mid"): R-MAT scale 20 (a, b, c = .57, .19, .19),
+8,388,608 unique edges of which 90% form G0, 8 vertex labels Zipf(1.2),
+20 six-vertex queries (10 sparse, 10 dense) from tests/golden/queries_mid.json,
+one batch of 90,000 insertions from the held-out pool + 10,000 uniform
+deletions, interleaved. Inputs are synthetic (the paper's datasets are not
+available). The graph (about 60 MB of adjacency) fits in L2, so L2 is flushed
+(a 256 MiB write) before every timed step, outside the timed events.
+
+value   = updates/s with the batch already in HBM (device events per step)
+e2e     = the same metric through the C-ABI with host (pinned) batch buffers
+roofline: the DFS kernel's algorithmic bytes (SURVEY-d accounting, counted by
+          an instrumented launch) / its measured duration, against the
+          measured HBM copy bandwidth
+cpu_baseline: the CPU oracle on a bounded sample of the same batch.
+--impl reference times that oracle alone, as the reference arm.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "mid": {"workload": "mid", "queries": "tests/golden/queries_mid.json", "n_ins": 90_000, "n_del": 10_000},
+    "tiny": {"workload": "tiny", "queries": None, "n_ins": 256, "n_del": 0},
+}
+METRIC = "updates/s & incremental matches/s per batch (1 GB300); p50/p99 batch latency"
+STATUS_BYTES = 104  # the library's status block, read back after staging and after matching
+
+
+def load_workload(name):
+    from paper_2401_17018_gb300 import inputs as I
+    spec = WORKLOADS[name]
+    w = I.make_workload(spec["workload"])
+    if spec["queries"]:
+        with open(os.path.join(ROOT, spec["queries"])) as f:
+            qd = json.load(f)
+        if qd.get("graph_digest") not in (None, w.graph.digest()):
+            raise SystemExit("stored queries were chosen on a different graph")
+        queries = [I.Query.from_json(x) for x in qd["queries"]]
+    else:
+        queries = [I.TRIANGLE_WITH_TAIL]
+    batch = I.workload_batch(w, spec["n_ins"], spec["n_del"])
+    return w, queries, batch
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dfs_traffic(kernel_file="paper_2401_17018_gb300/csrc/gm_match.cu"):
+    """DRAM bytes per DFS launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "dfs_mid_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    h = hashlib.sha256(open(os.path.join(ROOT, kernel_file), "rb").read()).hexdigest()[:16]
+    if d.get("source_sha") != h:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(w, queries, batch, budget_s=20.0):
+    """The oracle, single-threaded, on a sample of the batch's updates."""
+    from oracle import oracle as O
+    g = w.graph
+    t = time.perf_counter()
+    O.bdsm_multi(g.n, g.labels, g.src, g.dst, queries, batch, eval_idx=[])
+    setup = time.perf_counter() - t
+    stride = max(1, len(batch) // 50)
+    total_upd, total_s = 0, 0.0
+    start = 0
+    while total_s < budget_s and start < stride:
+        ev = np.arange(start, len(batch), stride)
+        t = time.perf_counter()
+        O.bdsm_multi(g.n, g.labels, g.src, g.dst, queries, batch, eval_idx=ev)
+        dt = time.perf_counter() - t - setup
+        total_upd += ev.size
+        total_s += max(dt, 1e-9)
+        start += 1
+    return {"value": total_upd / total_s, "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%d updates (every %d-th, offsets 0..%d) of the batch, all %d queries; "
+                      "graph build (%.1f s per call) excluded" % (total_upd, stride, start - 1, len(queries),
+                                                                    setup)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    w, queries, batch = load_workload(args.workload)
+    g = w.graph
+    stride = max(1, len(batch) // 20)
+    times, nupd = [], []
+    for step in range(args.warmup + args.steps):
+        ev = np.arange(step % stride, len(batch), stride)
+        t = time.perf_counter()
+        O.bdsm_multi(g.n, g.labels, g.src, g.dst, queries, batch, eval_idx=ev)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            times.append(dt)
+            nupd.append(ev.size)
+    v = sum(nupd) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": config_of(args.workload, len(batch), len(queries)),
+            "cpu_baseline": {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step %d updates (every %d-th) of the batch, all %d queries, "
+                                       "graph build included" % (nupd[0], stride, len(queries))},
+            "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(workload, b, nq):
+    spec = WORKLOADS[workload]
+    return {"workload": "%s: R-MAT %s, %d queries, batch %d (%d ins + %d del)" % (
+        workload, {"mid": "scale 20, 7.55M edges, 8 labels Zipf(1.2)",
+                   "tiny": "scale 11, 9k edges, 4 labels"}[workload], nq, b, spec["n_ins"], spec["n_del"]),
+        "batch_updates": b, "queries": nq, "l2": "flushed before every timed step (256 MiB write)",
+        "step": "apply batch (stage+seed+DFS+counts to host) + commit; batch and inverse alternate"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gamma", choices=["gamma", "reference"])
+    ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--per-query", action="store_true", help="plain form: one launch sequence per query")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2401_17018_gb300 import gamma as G
+
+    w, queries, batch = load_workload(args.workload)
+    inv = batch.inverse()
+    g = w.graph
+    stream = torch.cuda.Stream()
+    flags = G.GAMMA_F_PER_QUERY if args.per_query else 0
+    ctx = G.Context(device=local, stream=stream, flags=flags)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx.load_graph(g.n, dev(g.labels), dev(g.src), dev(g.dst))
+    qids = [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
+    b = len(batch)
+    d_b = (dev(batch.op), dev(batch.src), dev(batch.dst))
+    d_i = (dev(inv.op), dev(batch.src), dev(batch.dst))
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_b = (pin(batch.op), pin(batch.src), pin(batch.dst))
+    h_i = (pin(inv.op), pin(batch.src), pin(batch.dst))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    applied = [0]  # batches applied so far: even -> the graph is G0, odd -> G0 + batch
+
+    def step(k, bufs_b, bufs_i):
+        op, s, d = bufs_b if applied[0] % 2 == 0 else bufs_i
+        pos, neg = ctx.apply_batch(op, s, d, qids)
+        st = ctx.stats()
+        ctx.commit()
+        applied[0] += 1
+        return int(pos.sum()) + int(neg.sum()), st
+
+    for k in range(args.warmup):
+        step(k, d_b, d_i)
+    # instrumented step (untimed): algorithmic bytes of the DFS launch on the batch
+    if applied[0] % 2:
+        step(0, d_b, d_i)
+    ctx.set_options(flags=flags | G.GAMMA_F_COUNT_BYTES)
+    _, st_bytes = step(0, d_b, d_i)
+    step(0, d_b, d_i)
+    ctx.set_options(flags=flags)
+    alg_bytes = st_bytes["alg_bytes"]
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ctx.stats()["kernel_launches"]
+    matches, phases = [], []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            evs[k][0].record(stream)
+        m, st = step(k, d_b, d_i)
+        with torch.cuda.stream(stream):
+            evs[k][1].record(stream)
+        matches.append(m)
+        phases.append(st)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = ctx.stats()["kernel_launches"] - launches0
+    clk = clocks.stop()
+    ms = [a.elapsed_time(bb) for a, bb in evs]
+    tot_s = sum(ms) / 1e3
+    if dist:
+        t = torch.tensor([tot_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_s = float(t.item())
+        dist.barrier()
+
+    # end to end through the C-ABI with host (pinned) batch buffers
+    e2e_t = []
+    for k in range(args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        step(k, h_b, h_i)
+        e2e_t.append(time.perf_counter() - t)
+    e2e_v = world * b * args.steps / sum(e2e_t)
+
+    dfs_ms = statistics.mean(p["ms_match"] for p in phases)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (dfs_ms / 1e3) / 1e9 if dfs_ms > 0 else 0.0
+    phase_ms = {k: round(statistics.mean(p[k] for p in phases), 4)
+                for k in ("ms_stage", "ms_seed", "ms_match", "ms_finalize", "ms_commit")}
+    line = {
+        "metric": METRIC, "value": world * b * args.steps / tot_s, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": config_of(args.workload, b, len(queries)),
+        "matches_per_s": world * sum(matches) / tot_s,
+        "incremental_matches_per_step": matches[0],
+        "p50_ms": statistics.median(ms), "p99_ms": float(np.percentile(ms, 99)),
+        "phase_ms": phase_ms, "wall_s": wall,
+        "e2e": {"value": e2e_v, "unit": "updates/s", "h2d_bytes_per_step": 9 * b,
+                "d2h_bytes_per_step": 16 * len(queries) + 2 * STATUS_BYTES + 8},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "k_dfs", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": dfs_traffic(), "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes, "launch_ms": dfs_ms},
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, queries, batch)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

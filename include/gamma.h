@@ -56,6 +56,7 @@ extern "C" {
 #define GAMMA_F_NO_FILTER 0x2u   /* disable the neighbour-label-count candidate filter */
 #define GAMMA_F_PER_QUERY 0x4u   /* plain form: one seed+DFS launch sequence per query */
 #define GAMMA_F_GRAPH 0x8u       /* replay the match phase as a captured CUDA graph */
+#define GAMMA_F_COUNT_BYTES 0x10u /* count the DFS kernel's algorithmic bytes (gamma_stats.alg_bytes) */
 
 typedef struct gamma_ctx gamma_ctx;
 
@@ -93,6 +94,8 @@ typedef struct {
   int64_t pool_cap;    /* adjacency slots available */
   int64_t live_edges;  /* directed adjacency entries of the current graph */
   uint64_t expansions; /* 32-candidate expansion steps of the last apply */
+  uint64_t alg_bytes;  /* DFS algorithmic bytes of the last apply (GAMMA_F_COUNT_BYTES) */
+  uint64_t kernel_launches; /* kernels the library has launched in this process so far */
 } gamma_stats;
 
 /* Create a context on options->device (options may be NULL: defaults).

@@ -227,29 +227,37 @@ static int make_order(srch *S, int32_t a, int32_t b) {
 }
 
 /*
- * oracle_bdsm: incremental matches of one query for one batch.
+ * oracle_bdsm_multi: incremental matches of nq queries for one batch.
  *   graph G: n vertices with labels[n]; m undirected edges (src[e], dst[e])
  *            (duplicates merged; self-loops or bad ids -> OR_EINVAL, bad_index = -1)
- *   query Q: q <= 31 vertices, qlabels[q], eq edges (qsrc, qdst); must be connected
+ *   queries: query j has qn[j] <= 31 vertices with labels qlab + qlab_off[j],
+ *            qe[j] edges (qsrc/qdst + qe_off[j]); each must be connected
  *   batch:   b updates (op[k] = +1/-1, usrc[k], udst[k])
  *   eval:    n_eval update indices to evaluate (eval_idx == NULL: all b, in order)
- *   out_count[j]: number of incremental matches charged to update eval_idx[j]
- *   tuples:  if non-NULL, rows of (update, sign, phi[0..q-1]) up to tuple_cap rows;
- *            *n_tuples receives the number of rows produced (may exceed the cap)
- *   node_budget: 0 = unlimited, else OR_EBUDGET once that many candidates were tried
+ *   out_count[j * ne + i]: matches of query j charged to update eval_idx[i]
+ *   tuples:  (one query only) rows of (update, sign, phi[0..q-1]) up to tuple_cap
+ *            rows; *n_tuples receives the number of rows produced
+ *   node_budget: 0 = unlimited, else OR_EBUDGET once that many candidates were
+ *            tried for one query
  * Returns OR_OK, OR_EINVAL (bad_index = offending update), OR_EBUDGET, OR_ENOMEM.
  */
-int oracle_bdsm(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
-                int32_t q, const int32_t *qlabels, int32_t eq, const int32_t *qsrc, const int32_t *qdst,
-                int64_t b, const int8_t *op, const int32_t *usrc, const int32_t *udst,
-                int64_t n_eval, const int64_t *eval_idx, uint64_t *out_count,
-                int32_t *tuples, int64_t tuple_cap, int64_t *n_tuples,
-                uint64_t node_budget, int64_t *bad_index) {
+int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
+                      int32_t nq, const int32_t *qn, const int32_t *qlab, const int64_t *qlab_off,
+                      const int32_t *qe, const int32_t *qsrc, const int32_t *qdst, const int64_t *qe_off,
+                      int64_t b, const int8_t *op, const int32_t *usrc, const int32_t *udst,
+                      int64_t n_eval, const int64_t *eval_idx, uint64_t *out_count,
+                      int32_t *tuples, int64_t tuple_cap, int64_t *n_tuples,
+                      uint64_t node_budget, int64_t *bad_index) {
   if (bad_index) *bad_index = -1;
   if (n_tuples) *n_tuples = 0;
-  if (q < 2 || q > 31 || eq < 1) return OR_EINVAL;
-  for (int32_t e = 0; e < eq; e++)
-    if (qsrc[e] < 0 || qsrc[e] >= q || qdst[e] < 0 || qdst[e] >= q || qsrc[e] == qdst[e]) return OR_EINVAL;
+  if (nq < 0 || (tuples && nq != 1)) return OR_EINVAL;
+  for (int32_t j = 0; j < nq; j++) {
+    int32_t q = qn[j], eq = qe[j];
+    const int32_t *qs = qsrc + qe_off[j], *qd = qdst + qe_off[j];
+    if (q < 2 || q > 31 || eq < 1) return OR_EINVAL;
+    for (int32_t e = 0; e < eq; e++)
+      if (qs[e] < 0 || qs[e] >= q || qd[e] < 0 || qd[e] >= q || qs[e] == qd[e]) return OR_EINVAL;
+  }
 
   hmap gset, bmap;
   if (hmap_init(&gset, m) || hmap_init(&bmap, b)) return OR_ENOMEM;
@@ -293,35 +301,50 @@ int oracle_bdsm(int32_t n, const int32_t *labels, int64_t m, const int32_t *src,
   if (adj_build(&AG, n, mu, gs, gd) || adj_build(&AP, n, mp, ps, pd)) return OR_ENOMEM;
   free(ps); free(pd);
 
-  srch S;
-  memset(&S, 0, sizeof(S));
-  S.q = q; S.qlab = qlabels; S.eq = eq; S.qs = qsrc; S.qd = qdst; S.lab = labels;
-  S.gset = &gset; S.bmap = &bmap; S.op = op; S.budget = node_budget;
-  S.tuples = tuples; S.tuple_cap = tuple_cap; S.n_tuples = n_tuples;
-
   int rc = OR_OK;
   int64_t ne = eval_idx ? n_eval : b;
-  for (int64_t j = 0; j < ne && rc == OR_OK; j++) {
-    int64_t i = eval_idx ? eval_idx[j] : j;
-    if (i < 0 || i >= b) { rc = OR_EINVAL; break; }
-    S.sign = op[i]; S.upd = i; S.view = (op[i] == 1) ? &AP : &AG;
-    S.count = 0;
-    for (int32_t e = 0; e < eq; e++) {
-      for (int o = 0; o < 2; o++) {
-        int32_t a = qsrc[e], bq = qdst[e];
-        int32_t x = o ? udst[i] : usrc[i], y = o ? usrc[i] : udst[i];
-        if (labels[x] != qlabels[a] || labels[y] != qlabels[bq]) continue;
-        if (!make_order(&S, a, bq)) { rc = OR_EINVAL; break; }
-        memset(S.used_q, 0, sizeof(S.used_q));
-        S.phi[a] = x; S.phi[bq] = y; S.used_q[a] = S.used_q[bq] = 1;
-        extend(&S, 2);
-        if (S.over_budget) { rc = OR_EBUDGET; break; }
+  for (int32_t j = 0; j < nq && rc == OR_OK; j++) {
+    srch S;
+    memset(&S, 0, sizeof(S));
+    S.q = qn[j]; S.qlab = qlab + qlab_off[j]; S.eq = qe[j];
+    S.qs = qsrc + qe_off[j]; S.qd = qdst + qe_off[j]; S.lab = labels;
+    S.gset = &gset; S.bmap = &bmap; S.op = op; S.budget = node_budget;
+    S.tuples = tuples; S.tuple_cap = tuple_cap; S.n_tuples = n_tuples;
+    for (int64_t i = 0; i < ne && rc == OR_OK; i++) {
+      int64_t k = eval_idx ? eval_idx[i] : i;
+      if (k < 0 || k >= b) { rc = OR_EINVAL; break; }
+      S.sign = op[k]; S.upd = k; S.view = (op[k] == 1) ? &AP : &AG;
+      S.count = 0;
+      for (int32_t e = 0; e < S.eq; e++) {
+        for (int o = 0; o < 2; o++) {
+          int32_t a = S.qs[e], bq = S.qd[e];
+          int32_t x = o ? udst[k] : usrc[k], y = o ? usrc[k] : udst[k];
+          if (labels[x] != S.qlab[a] || labels[y] != S.qlab[bq]) continue;
+          if (!make_order(&S, a, bq)) { rc = OR_EINVAL; break; }
+          memset(S.used_q, 0, sizeof(S.used_q));
+          S.phi[a] = x; S.phi[bq] = y; S.used_q[a] = S.used_q[bq] = 1;
+          extend(&S, 2);
+          if (S.over_budget) { rc = OR_EBUDGET; break; }
+        }
+        if (rc != OR_OK) break;
       }
-      if (rc != OR_OK) break;
+      if (out_count) out_count[(int64_t)j * ne + i] = S.count;
     }
-    if (out_count) out_count[j] = S.count;
   }
   adj_free(&AG); adj_free(&AP);
   hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd);
   return rc;
+}
+
+/* One query: oracle_bdsm_multi with nq = 1. */
+int oracle_bdsm(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
+                int32_t q, const int32_t *qlabels, int32_t eq, const int32_t *qsrc, const int32_t *qdst,
+                int64_t b, const int8_t *op, const int32_t *usrc, const int32_t *udst,
+                int64_t n_eval, const int64_t *eval_idx, uint64_t *out_count,
+                int32_t *tuples, int64_t tuple_cap, int64_t *n_tuples,
+                uint64_t node_budget, int64_t *bad_index) {
+  int64_t zero = 0;
+  return oracle_bdsm_multi(n, labels, m, src, dst, 1, &q, qlabels, &zero, &eq, qsrc, qdst, &zero, b, op, usrc,
+                           udst, n_eval, eval_idx, out_count, tuples, tuple_cap, n_tuples, node_budget,
+                           bad_index);
 }

@@ -66,6 +66,14 @@ def _load():
             ctypes.c_int64, p, p,
             p, ctypes.c_int64, p,
             ctypes.c_uint64, p]
+        lib.oracle_bdsm_multi.restype = ctypes.c_int
+        lib.oracle_bdsm_multi.argtypes = [
+            ctypes.c_int32, p, ctypes.c_int64, p, p,
+            ctypes.c_int32, p, p, p, p, p, p, p,
+            ctypes.c_int64, p, p, p,
+            ctypes.c_int64, p, p,
+            p, ctypes.c_int64, p,
+            ctypes.c_uint64, p]
         _lib = lib
     return _lib
 
@@ -122,6 +130,38 @@ def bdsm(n: int, labels, src, dst, query, batch, eval_idx: Optional[Sequence[int
             raise OracleError(ENOMEM, -1)
         tup = tup[:nt.value]
     return counts, tup
+
+
+def bdsm_multi(n: int, labels, src, dst, queries, batch, eval_idx: Optional[Sequence[int]] = None,
+               budget: int = 0) -> np.ndarray:
+    """O2 for several queries in one call (G, G' and the batch map are built
+    once). Returns counts[j, i] = matches of query j charged to update eval_idx[i]."""
+    lib = _load()
+    labels = np.ascontiguousarray(labels, np.int32)
+    src = np.ascontiguousarray(src, np.int32)
+    dst = np.ascontiguousarray(dst, np.int32)
+    qn = np.array([q.q for q in queries], np.int32)
+    qe = np.array([q.eq for q in queries], np.int32)
+    ql = np.ascontiguousarray(np.concatenate([q.labels for q in queries]) if queries else np.zeros(1), np.int32)
+    qs = np.ascontiguousarray(np.concatenate([q.src for q in queries]) if queries else np.zeros(1), np.int32)
+    qd = np.ascontiguousarray(np.concatenate([q.dst for q in queries]) if queries else np.zeros(1), np.int32)
+    lo = np.concatenate([[0], np.cumsum(qn)[:-1]]).astype(np.int64) if queries else np.zeros(1, np.int64)
+    eo = np.concatenate([[0], np.cumsum(qe)[:-1]]).astype(np.int64) if queries else np.zeros(1, np.int64)
+    op = np.ascontiguousarray(batch.op, np.int8)
+    us = np.ascontiguousarray(batch.src, np.int32)
+    ud = np.ascontiguousarray(batch.dst, np.int32)
+    b = op.size
+    ev = None if eval_idx is None else np.ascontiguousarray(eval_idx, np.int64)
+    ne = b if ev is None else ev.size
+    counts = np.zeros(max(len(queries) * ne, 1), np.uint64)
+    bad = ctypes.c_int64(-1)
+    rc = lib.oracle_bdsm_multi(n, _ptr(labels), src.size, _ptr(src), _ptr(dst),
+                               len(queries), _ptr(qn), _ptr(ql), _ptr(lo), _ptr(qe), _ptr(qs), _ptr(qd), _ptr(eo),
+                               b, _ptr(op), _ptr(us), _ptr(ud), ne, _ptr(ev), _ptr(counts),
+                               None, 0, None, budget, ctypes.byref(bad))
+    if rc != OK:
+        raise OracleError(rc, bad.value)
+    return counts[:len(queries) * ne].reshape(len(queries), ne)
 
 
 def totals(counts: np.ndarray, op: np.ndarray, eval_idx=None) -> Tuple[int, int]:

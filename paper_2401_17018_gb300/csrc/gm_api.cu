@@ -13,6 +13,7 @@
 #include "gm_graph.cuh"
 
 static thread_local char g_cuda_msg[512];
+unsigned long long gm_launch_count = 0;
 
 int gm_cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
   snprintf(g_cuda_msg, sizeof(g_cuda_msg), "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e),
@@ -332,6 +333,7 @@ int run_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_strid
     // clear the match part of the status (err/abort and nseeds..rows)
     CKC(cudaMemsetAsync(&ctx->d_st->err, 0, 2 * sizeof(int32_t), s));
     CKC(cudaMemsetAsync(&ctx->d_st->nseeds, 0, 5 * sizeof(uint64_t), s));
+    CKC(cudaMemsetAsync(&ctx->d_st->alg_bytes, 0, sizeof(uint64_t), s));
     CKC(cudaEventRecord(ctx->ev[2], s));
     MatchArgs a;
     a.g = ctx->gd();
@@ -345,6 +347,7 @@ int run_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_strid
     a.budget = ctx->budget;
     a.tile = ctx->tile;
     a.warps_per_block = ctx->wpb;
+    a.count_bytes = (ctx->flags & GAMMA_F_COUNT_BYTES) ? 1 : 0;
     a.st = ctx->d_st;
     a.plans = ctx->d_plans; a.nplans = ctx->nplans;
     a.pair_plans = ctx->d_pair_plans;
@@ -379,6 +382,7 @@ int run_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_strid
     ctx->stats.seeds = (int64_t)st.nseeds;
     ctx->stats.work_items = (int64_t)st.nitems;
     ctx->stats.expansions = st.expansions;
+    ctx->stats.alg_bytes = st.alg_bytes;
     return GAMMA_OK;
   }
   return ctx->fail(GAMMA_ENOMEM, "work item buffer kept overflowing");
@@ -807,6 +811,7 @@ int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out) {
   out->pool_used = (int64_t)ctx->pool_top;
   out->pool_cap = ctx->pool_cap;
   out->live_edges = ctx->live;
+  out->kernel_launches = __atomic_load_n(&gm_launch_count, __ATOMIC_RELAXED);
   return GAMMA_OK;
 }
 

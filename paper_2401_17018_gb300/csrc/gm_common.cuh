@@ -33,7 +33,8 @@ struct GmStatus {
   uint64_t next_item;     // DFS scheduling cursor
   uint64_t expansions;    // 32-wide expansion steps done
   uint64_t rows;          // match rows produced (may exceed capacity)
-  uint64_t live;          // directed entries of the committed graph
+  uint64_t live;          // change of directed entries at commit
+  uint64_t alg_bytes;     // DFS algorithmic bytes (instrumented mode)
   uint64_t garbage;       // slots freed by relocation
   uint32_t max_label;     // load: largest vertex label
   uint32_t pad2;
@@ -117,6 +118,10 @@ __device__ __forceinline__ void gm_bad_index(GmStatus *st, int64_t k) {
   } while (0)
 
 int gm_cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+// kernels launched by the library in this process (read into gamma_stats)
+extern unsigned long long gm_launch_count;
+#define GM_LAUNCHED() __atomic_add_fetch(&gm_launch_count, 1ull, __ATOMIC_RELAXED)
 
 // primitives (gm_prims.cu)
 int gm_scan_excl_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);

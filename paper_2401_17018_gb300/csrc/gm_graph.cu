@@ -365,6 +365,7 @@ inline int grid_for(int64_t n, int threads) {
 int gm_load_validate(const int32_t *labels, int32_t n, const int32_t *src, const int32_t *dst, int64_t m,
                      GmStatus *st, cudaStream_t s) {
   k_load_validate<<<grid_for(n > m ? n : m, 256), 256, 0, s>>>(labels, n, src, dst, m, st);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   return GAMMA_OK;
 }
@@ -385,10 +386,12 @@ int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m,
   GM_CUDA(cudaMemsetAsync(deg, 0, sizeof(uint32_t) * (g.n + 1), s));
   if (m > 0) {
     k_load_keys<<<grid_for(m, 256), 256, 0, s>>>(src, dst, m, g.label, g.idb, keys);
+    GM_LAUNCHED();
     GM_CUDA(cudaGetLastError());
     int rc = gm_radix_sort(keys, nullptr, tk, nullptr, n2, 1, 32 + g.idb, s);
     if (rc) return rc;
     k_load_uniq<<<grid_for(n2, 256), 256, 0, s>>>(keys, n2, flag, deg);
+    GM_LAUNCHED();
     GM_CUDA(cudaGetLastError());
     rc = gm_scan_excl_u32(flag, pos, n2, s);
     if (rc) return rc;
@@ -396,10 +399,12 @@ int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m,
   int rc = gm_scan_excl_u32(deg, rowstart, g.n, s);
   if (rc) return rc;
   k_load_caps<<<grid_for(g.n, 256), 256, 0, s>>>(deg, g.n, g.cap);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   rc = gm_scan_excl_u32(g.cap, off, g.n, s);
   if (rc) return rc;
   k_load_adj<<<grid_for(g.n, 256), 256, 0, s>>>(off, deg, g.cap, g.n, g.adj, st);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   GM_CUDA(cudaMemcpyAsync(h_st, st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
   GM_CUDA(cudaStreamSynchronize(s));
@@ -411,6 +416,7 @@ int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m,
   GM_CUDA(cudaMalloc((void **)&etag, sizeof(uint32_t) * cap));
   if (m > 0) {
     k_load_scatter<<<grid_for(n2, 256), 256, 0, s>>>(keys, n2, flag, pos, rowstart, off, col);
+    GM_LAUNCHED();
     GM_CUDA(cudaGetLastError());
   }
   GM_CUDA(cudaFreeAsync(keys, s));
@@ -432,6 +438,7 @@ int gm_nlf(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32
   int64_t blocks = ((int64_t)nverts_max * 32 + threads - 1) / threads;
   if (blocks > 8192) blocks = 8192;
   k_nlf<<<(int)blocks, threads, 0, s>>>(g, verts, nverts_dev, nverts_max);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   return GAMMA_OK;
 }
@@ -440,24 +447,30 @@ int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *ds
              GmStatus *st, cudaStream_t s) {
   const int64_t n2 = 2 * b;
   k_stage_prep<<<grid_for(b, 256), 256, 0, s>>>(op, src, dst, b, g, sb.cu, sb.cv, sb.cop, sb.keys, sb.vals, st);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   int rc = gm_radix_sort(sb.keys, sb.vals, sb.tk, sb.tv, n2, 1, 33 + g.idb, s);
   if (rc) return rc;
   k_stage_check<<<grid_for(n2, 256), 256, 0, s>>>(sb.keys, sb.vals, n2, g, sb.head, st);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   rc = gm_scan_excl_u32(sb.head, sb.gid, n2, s);
   if (rc) return rc;
   GM_CUDA(cudaMemsetAsync(sb.gins, 0, sizeof(uint32_t) * n2, s));
   k_stage_groups<<<grid_for(n2, 256), 256, 0, s>>>(sb.keys, n2, sb.head, sb.gid, sb.gv, sb.gstart, sb.gins, st);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   k_stage_plan<<<grid_for(n2, 256), 256, 0, s>>>(g, sb.gv, sb.gins, sb.greloc, st);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   k_stage_alloc<<<1, 32, 0, s>>>(g, st);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   int64_t mb = (n2 * 32 + 255) / 256;
   if (mb > 16384) mb = 16384;
   if (mb < 1) mb = 1;
   k_stage_merge<<<(int)mb, 256, 0, s>>>(g, sb.keys, sb.vals, n2, sb.gv, sb.gstart, sb.gins, sb.greloc, sb.bkeys, st);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   return gm_nlf(g, sb.gv, &st->ntouched, (uint32_t)n2, s);
 }
@@ -468,12 +481,14 @@ int gm_commit(GraphDev g, const StageBufs &sb, int64_t b, GmStatus *st, cudaStre
   if (mb > 16384) mb = 16384;
   if (mb < 1) mb = 1;
   k_commit<<<(int)mb, 256, 0, s>>>(g, sb.gv, sb.gins, st);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   return gm_nlf(g, sb.gv, &st->ntouched, (uint32_t)n2, s);
 }
 
 int gm_begin_group(GmStatus *st, cudaStream_t s) {
   k_begin_group<<<1, 32, 0, s>>>(st);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   return GAMMA_OK;
 }

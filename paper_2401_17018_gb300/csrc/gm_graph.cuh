@@ -50,6 +50,7 @@ struct MatchArgs {
   int tile;                    // DFS frontier tile
   int nlev;                    // stored DFS levels (max q - 3, >= 1)
   int warps_per_block;
+  int count_bytes;             // accumulate algorithmic bytes into st->alg_bytes
   GmStatus *st;
 };
 

@@ -40,9 +40,17 @@ __device__ __forceinline__ bool tag_ok(uint32_t t, uint32_t sdel, uint32_t upd) 
 
 // is the edge (w, c) visible in the seed's view under the charging rule?
 // x = adjacency key of c (flag bit ignored)
+// algorithmic bytes of one binary search over a list of d entries: one 32-B
+// sector per halving step, never more than the whole list
+__device__ __forceinline__ uint32_t probe_bytes(uint32_t d) {
+  uint32_t steps = 32u - __clz(d | 1u);
+  return min(4u * d, 32u * steps) + 8u;
+}
+
 __device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t x, uint32_t sdel,
-                                        uint32_t upd) {
+                                        uint32_t upd, uint64_t &bytes) {
   const uint2 a = __ldg(reinterpret_cast<const uint2 *>(g.adj) + w);
+  bytes += probe_bytes(a.y);
   const uint32_t *L = g.col + a.x;
   const uint32_t key = x & ~1u;
   uint32_t p = gm_lower_bound(L, a.y, key);
@@ -231,6 +239,7 @@ __global__ void k_dfs(MatchArgs a) {
     const uint32_t m0 = __ldg(a.cu + upd), m1 = __ldg(a.cv + upd);
     const uint32_t sdel = a.op[upd] < 0 ? 1u : 0u;
     uint64_t wcount = 0;
+    uint64_t lbytes = 0;  // this lane's algorithmic bytes (only reported with count_bytes)
     uint32_t chunks = 0;
     int lev = -1;            // parent level (-1 = the seed itself)
     uint32_t root_cur = 0;
@@ -268,10 +277,12 @@ __global__ void k_dfs(MatchArgs a) {
             uint32_t c = __ldg(g.nlf + (size_t)m0 * g.nlfw + lab);
             if (c < best) { best = c; bestv = m0; drv = 0; }
           }
+          lbytes += 4u * __popc(bw);
           if (best > 0) {
             uint2 ad = __ldg(reinterpret_cast<const uint2 *>(g.adj) + bestv);
             uint32_t slo, shi;
             seg_bounds(g, g.col + ad.x, ad.y, lab, slo, shi);
+            lbytes += 2u * probe_bytes(ad.y);
             lo = ad.x + slo;
             len = shi - slo;
           }
@@ -341,15 +352,16 @@ __global__ void k_dfs(MatchArgs a) {
           const int pos = l2 + 2;
           const uint32_t vv = V[l2 * T + ee];
           if ((chk_neq >> pos) & 1) ok = (vv != id);
-          if (ok && ((chk_edge >> pos) & 1)) ok = edge_ok(g, vv, x, sdel, upd);
+          if (ok && ((chk_edge >> pos) & 1)) ok = edge_ok(g, vv, x, sdel, upd, lbytes);
           ee = PAR[l2 * T + ee];
         }
         if (ok && ((chk_neq >> 1) & 1)) ok = (m1 != id);
-        if (ok && ((chk_edge >> 1) & 1)) ok = edge_ok(g, m1, x, sdel, upd);
+        if (ok && ((chk_edge >> 1) & 1)) ok = edge_ok(g, m1, x, sdel, upd, lbytes);
         if (ok && (chk_neq & 1)) ok = (m0 != id);
-        if (ok && (chk_edge & 1)) ok = edge_ok(g, m0, x, sdel, upd);
+        if (ok && (chk_edge & 1)) ok = edge_ok(g, m0, x, sdel, upd, lbytes);
       }
       if (ok && stored && a.use_filter) ok = nlf_ok(g, id, P, c);
+      if (gidx < total) lbytes += ((x & 1u) ? 8u : 4u) + (ok ? 8u : 0u);
       const unsigned mask = __ballot_sync(GM_FULL, ok);
       if (!stored) {
         wcount += __popc(mask);
@@ -394,6 +406,11 @@ __global__ void k_dfs(MatchArgs a) {
       }
       if ((chunks & 1023u) == 0 && warp_read(&st->abort)) break;
     }
+    if (a.count_bytes) {
+      lbytes += (lane == 0) ? sizeof(WorkItem) : 0;
+      for (int d = 16; d > 0; d >>= 1) lbytes += __shfl_down_sync(GM_FULL, lbytes, d);
+      if (lane == 0) atomicAdd((unsigned long long *)&st->alg_bytes, (unsigned long long)lbytes);
+    }
     if (lane == 0) {
       if (wcount) {
         atomicAdd((unsigned long long *)&a.cnt[P.qslot * 2 + sdel], (unsigned long long)wcount);
@@ -420,6 +437,7 @@ int gm_seed(const MatchArgs &a, cudaStream_t s) {
   int64_t blocks = (a.b + threads - 1) / threads;
   if (blocks > 65536) blocks = 65536;
   k_seed<<<(int)blocks, threads, 0, s>>>(a);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   return GAMMA_OK;
 }
@@ -436,6 +454,7 @@ int gm_dfs(const MatchArgs &a, int num_sms, cudaStream_t s) {
   GM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfs, wpb * 32, smem));
   if (per_sm < 1) return GAMMA_EINVAL;
   k_dfs<<<num_sms * per_sm, wpb * 32, smem, s>>>(a);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   return GAMMA_OK;
 }

@@ -72,16 +72,19 @@ int scan_excl(const T *in, T *out, int64_t n, cudaStream_t s) {
   int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb == 1) {
     k_scan_tile<T><<<1, SCAN_THREADS, 0, s>>>(in, out, n, (T *)nullptr);
+    GM_LAUNCHED();
     GM_CUDA(cudaGetLastError());
     return GAMMA_OK;
   }
   T *part = nullptr;
   GM_CUDA(cudaMallocAsync((void **)&part, sizeof(T) * nb, s));
   k_scan_tile<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, part);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   int rc = scan_excl<T>(part, part, nb, s);
   if (rc) { cudaFreeAsync(part, s); return rc; }
   k_scan_add<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(out, n, part);
+  GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   GM_CUDA(cudaFreeAsync(part, s));
   return GAMMA_OK;
@@ -182,6 +185,7 @@ int gm_radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *tk, uint32_t *tv, in
   int passes = 0;
   for (int shift = b0; shift < b1; shift += 8, passes++) {
     k_rs_hist<<<nb, RS_THREADS, 0, s>>>(ka, n, shift, counts, nb);
+    GM_LAUNCHED();
     GM_CUDA(cudaGetLastError());
     int rc = gm_scan_excl_u32(counts, counts, (int64_t)256 * nb, s);
     if (rc) return rc;
@@ -189,6 +193,7 @@ int gm_radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *tk, uint32_t *tv, in
       k_rs_scatter<true><<<nb, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, counts, nb);
     else
       k_rs_scatter<false><<<nb, RS_THREADS, 0, s>>>(ka, nullptr, kb, nullptr, n, shift, counts, nb);
+    GM_LAUNCHED();
     GM_CUDA(cudaGetLastError());
     uint64_t *tk2 = ka; ka = kb; kb = tk2;
     uint32_t *tv2 = va; va = vb; vb = tv2;

@@ -19,7 +19,8 @@ from . import build as _build
 
 GAMMA_OK, GAMMA_EINVAL, GAMMA_ENOMEM, GAMMA_ESTATE, GAMMA_EOVERFLOW, GAMMA_ETIMEOUT, GAMMA_ECUDA = (
     0, -1, -2, -3, -4, -5, -6)
-GAMMA_F_PER_UPDATE, GAMMA_F_NO_FILTER, GAMMA_F_PER_QUERY, GAMMA_F_GRAPH = 0x1, 0x2, 0x4, 0x8
+GAMMA_F_PER_UPDATE, GAMMA_F_NO_FILTER, GAMMA_F_PER_QUERY, GAMMA_F_GRAPH, GAMMA_F_COUNT_BYTES = (
+    0x1, 0x2, 0x4, 0x8, 0x10)
 
 _NAMES = {0: "GAMMA_OK", -1: "GAMMA_EINVAL", -2: "GAMMA_ENOMEM", -3: "GAMMA_ESTATE",
           -4: "GAMMA_EOVERFLOW", -5: "GAMMA_ETIMEOUT", -6: "GAMMA_ECUDA"}
@@ -40,7 +41,8 @@ class gamma_stats(ctypes.Structure):
     _fields_ = [("ms_stage", ctypes.c_double), ("ms_seed", ctypes.c_double), ("ms_match", ctypes.c_double),
                 ("ms_finalize", ctypes.c_double), ("ms_commit", ctypes.c_double), ("seeds", ctypes.c_int64),
                 ("work_items", ctypes.c_int64), ("touched", ctypes.c_int64), ("pool_used", ctypes.c_int64),
-                ("pool_cap", ctypes.c_int64), ("live_edges", ctypes.c_int64), ("expansions", ctypes.c_uint64)]
+                ("pool_cap", ctypes.c_int64), ("live_edges", ctypes.c_int64), ("expansions", ctypes.c_uint64),
+                ("alg_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
 
 
 class GammaError(RuntimeError):
