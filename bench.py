@@ -43,7 +43,7 @@ WORKLOADS = {
     "tiny": {"workload": "tiny", "queries": None, "n_ins": 256, "n_del": 0},
 }
 METRIC = "updates/s & incremental matches/s per batch (1 GB300); p50/p99 batch latency"
-STATUS_BYTES = 104  # the library's status block, read back after staging and after matching
+STATUS_BYTES = 104  # the library's status block, read back after staging, matching and commit
 
 
 def load_workload(name):
@@ -315,7 +315,7 @@ def main():
         "p50_ms": statistics.median(ms), "p99_ms": float(np.percentile(ms, 99)),
         "phase_ms": phase_ms, "wall_s": wall,
         "e2e": {"value": e2e_v, "unit": "updates/s", "h2d_bytes_per_step": 9 * b,
-                "d2h_bytes_per_step": 16 * len(queries) + 2 * STATUS_BYTES + 8},
+                "d2h_bytes_per_step": 16 * len(queries) + 3 * STATUS_BYTES},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": "k_dfs", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": dfs_traffic(), "peak_kind": peak_kind,

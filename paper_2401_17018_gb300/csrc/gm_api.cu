@@ -70,6 +70,13 @@ struct gamma_ctx {
   uint2 *d_adj = nullptr;
   uint32_t *d_cap = nullptr, *d_col = nullptr, *d_etag = nullptr;
   uint8_t *d_nlf = nullptr;
+  int32_t *d_hub_id = nullptr;
+  uint32_t *d_hub_lofs = nullptr;
+  uint2 *d_hub_tab = nullptr;
+  uint32_t *d_hub_keys = nullptr;
+  uint32_t hub_keys_cap = 0;
+  uint64_t hub_top = 0;
+  int32_t nhub = 0;
   uint32_t pool_cap = 0;
   uint64_t pool_top = 0;
   int64_t live = 0;
@@ -105,6 +112,12 @@ struct gamma_ctx {
   int64_t per_upd_cap = 0;
   int32_t *d_rows = nullptr;
   int64_t rows_cap = 0;
+  uint32_t *d_sched = nullptr;
+  int64_t sched_cap = 0;
+  Task *d_tasks = nullptr;
+  int64_t tasks_cap = 0;
+  uint32_t *d_task_seq = nullptr;
+  int64_t task_seq_cap = 0;
 
   GmStatus *d_st = nullptr;
   GmStatus *h_st = nullptr;       // pinned
@@ -116,6 +129,8 @@ struct gamma_ctx {
   GraphDev gd() const {
     GraphDev g;
     g.label = d_label; g.adj = d_adj; g.cap = d_cap; g.col = d_col; g.etag = d_etag; g.nlf = d_nlf;
+    g.hub_id = d_hub_id; g.hub_lofs = d_hub_lofs; g.hub_tab = d_hub_tab; g.hub_keys = d_hub_keys;
+    g.hub_keys_cap = hub_keys_cap; g.nhub = nhub;
     g.n = n; g.idb = idb; g.nlab = nlab; g.nlfw = nlfw;
     g.idmask = (idb >= 32) ? 0xffffffffu : ((1u << idb) - 1u);
     g.pool_cap = pool_cap;
@@ -149,8 +164,11 @@ namespace {
 void free_graph(gamma_ctx *ctx) {
   cudaFree(ctx->d_label); cudaFree(ctx->d_adj); cudaFree(ctx->d_cap);
   cudaFree(ctx->d_col); cudaFree(ctx->d_etag); cudaFree(ctx->d_nlf);
+  cudaFree(ctx->d_hub_id); cudaFree(ctx->d_hub_lofs); cudaFree(ctx->d_hub_tab); cudaFree(ctx->d_hub_keys);
   ctx->d_label = nullptr; ctx->d_adj = nullptr; ctx->d_cap = nullptr;
   ctx->d_col = nullptr; ctx->d_etag = nullptr; ctx->d_nlf = nullptr;
+  ctx->d_hub_id = nullptr; ctx->d_hub_lofs = nullptr; ctx->d_hub_tab = nullptr; ctx->d_hub_keys = nullptr;
+  ctx->nhub = 0; ctx->hub_keys_cap = 0; ctx->hub_top = 0;
   ctx->loaded = false;
   ctx->staged = false;
 }
@@ -302,6 +320,7 @@ void reset_status_host(gamma_ctx *ctx) {
   memset(ctx->h_st, 0, sizeof(GmStatus));
   ctx->h_st->bad_index = INT64_MAX;
   ctx->h_st->pool_top = (uint32_t)ctx->pool_top;
+  ctx->h_st->hub_top = (uint32_t)ctx->hub_top;
 }
 
 float ev_ms(cudaEvent_t a, cudaEvent_t b) {
@@ -325,6 +344,11 @@ int run_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_strid
     ctx->h_cnt_cap = 2 * std::max(nq, 1);
   }
   if (ctx->items_cap == 0) CK(ensure(ctx->d_items, ctx->items_cap, std::max<int64_t>(1 << 20, 8 * b)));
+  if (ctx->tasks_cap == 0) {
+    CK(ensure(ctx->d_tasks, ctx->tasks_cap, (int64_t)1 << 20));
+    CK(ensure(ctx->d_task_seq, ctx->task_seq_cap, ctx->tasks_cap));
+    CK(ensure(ctx->d_sched, ctx->sched_cap, GM_SCHED_WORDS));
+  }
   for (int attempt = 0; attempt < 4; attempt++) {
     cudaStream_t s = ctx->stream;
     CKC(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(uint64_t) * 2 * std::max(nq, 1), s));
@@ -348,6 +372,11 @@ int run_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_strid
     a.tile = ctx->tile;
     a.warps_per_block = ctx->wpb;
     a.count_bytes = (ctx->flags & GAMMA_F_COUNT_BYTES) ? 1 : 0;
+    a.tasks = ctx->d_tasks;
+    a.sched = ctx->d_sched;
+    a.task_seq = ctx->d_task_seq;
+    a.task_cap = (uint32_t)ctx->tasks_cap;
+    a.idle_limit_ns = 60ull * 1000000000ull;
     a.st = ctx->d_st;
     a.plans = ctx->d_plans; a.nplans = ctx->nplans;
     a.pair_plans = ctx->d_pair_plans;
@@ -360,6 +389,7 @@ int run_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_strid
       a.pair_off = ctx->d_pair_off + (size_t)gi * (np + 1);
       if (per_query) CK(gm_begin_group(ctx->d_st, s));
       CK(gm_seed(a, s));
+      CKC(cudaMemsetAsync(ctx->d_task_seq, 0, sizeof(uint32_t) * ctx->tasks_cap, s));
       if (!per_query) { CKC(cudaEventRecord(ctx->ev[3], s)); seeded = true; }
       CK(gm_dfs(a, ctx->num_sms, s));
     }
@@ -469,7 +499,7 @@ void gamma_destroy(gamma_ctx *ctx) {
   void *ps[] = {sb.cu, sb.cv, sb.cop, sb.keys, sb.tk, sb.vals, sb.tv, sb.head, sb.gid, sb.gv, sb.gstart,
                 sb.gins, sb.greloc, sb.bkeys, ctx->d_in_op, ctx->d_in_src, ctx->d_in_dst, ctx->d_plans,
                 ctx->d_pair_off, ctx->d_pair_plans, ctx->d_items, ctx->d_cnt, ctx->d_per_upd, ctx->d_rows,
-                ctx->d_st};
+                ctx->d_tasks, ctx->d_task_seq, ctx->d_sched, ctx->d_st};
   for (void *p : ps) if (p) cudaFree(p);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
   if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
@@ -578,6 +608,42 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
     int64_t live = 0;
     for (auto &a : hadj) live += a.y;
     ctx->live = live;
+  }
+  // hub index for long lists (label-segment starts + hash sets of the keys)
+  {
+    std::vector<int32_t> hid(n, -1);
+    uint64_t slots = 0;
+    int32_t nh = 0;
+    for (int32_t v = 0; v < n; v++) {
+      if (hadj[v].y >= GM_HUB_MIN) {
+        hid[v] = nh++;
+        uint64_t c = 8;
+        while (c < 3ull * hadj[v].y + 8) c <<= 1;
+        slots += c;
+      }
+    }
+    ctx->nhub = nh;
+    CKC(cudaMalloc((void **)&ctx->d_hub_id, sizeof(int32_t) * n));
+    CKC(cudaMemcpy(ctx->d_hub_id, hid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    if (nh > 0) {
+      CKC(cudaMalloc((void **)&ctx->d_hub_lofs, sizeof(uint32_t) * (size_t)nh * (ctx->nlab + 1)));
+      CKC(cudaMalloc((void **)&ctx->d_hub_tab, sizeof(uint2) * (size_t)nh));
+      CKC(cudaMemset(ctx->d_hub_tab, 0, sizeof(uint2) * (size_t)nh));
+      // keys need their top bit free for the empty marker
+      if (1 + ctx->idb + lb < 32) {
+        uint64_t cap = 2 * slots + (1u << 20);
+        if (cap > 0xF0000000ull) cap = 0xF0000000ull;
+        CKC(cudaMalloc((void **)&ctx->d_hub_keys, sizeof(uint32_t) * cap));
+        ctx->hub_keys_cap = (uint32_t)cap;
+      }
+      ctx->hub_top = 0;
+      reset_status_host(ctx);
+      CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
+      CK(gm_hub(ctx->gd(), nullptr, nullptr, (uint32_t)n, ctx->d_st, s));
+      CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
+      CKC(cudaStreamSynchronize(s));
+      ctx->hub_top = ctx->h_st->hub_top;
+    }
   }
   ctx->loaded = true;
   ctx->staged = false;
@@ -709,6 +775,7 @@ int gamma_apply_batch(gamma_ctx *ctx, int64_t b, const int8_t *op, const int32_t
   if (st0.err) return ctx->fail(st0.err, "gamma_apply_batch: staging failed (code %d)", st0.err);
   ctx->stats.ms_stage = ev_ms(ctx->ev[0], ctx->ev[1]);
   ctx->pool_top = st0.pool_top;
+  ctx->hub_top = st0.hub_top;
   ctx->stats.touched = st0.ntouched;
   ctx->b = b;
   ctx->staged = true;
@@ -767,9 +834,10 @@ int gamma_commit(gamma_ctx *ctx) {
   CKC(cudaEventRecord(ctx->ev[6], s));
   if (ctx->b > 0) CK(gm_commit(ctx->gd(), ctx->sb, ctx->b, ctx->d_st, s));
   CKC(cudaEventRecord(ctx->ev[7], s));
-  CKC(cudaMemcpyAsync(&ctx->h_st->live, &ctx->d_st->live, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
   CKC(cudaStreamSynchronize(s));
   ctx->live += (int64_t)ctx->h_st->live;  // signed change, two's complement
+  ctx->hub_top = ctx->h_st->hub_top;
   ctx->stats.ms_commit = ev_ms(ctx->ev[6], ctx->ev[7]);
   ctx->staged = false;
   return GAMMA_OK;

@@ -16,6 +16,8 @@
 #include "../../include/gamma.h"
 
 #define GM_MAXQ 16
+#define GM_HUB_MIN 128          // list length that makes a vertex a hub at load
+#define GM_EMPTY 0x80000000u    // empty hash slot (keys use at most 31 bits when hashing is on)
 #define GM_FULL 0xffffffffu
 
 // ---------------------------------------------------------------------------
@@ -37,8 +39,14 @@ struct GmStatus {
   uint64_t alg_bytes;     // DFS algorithmic bytes (instrumented mode)
   uint64_t garbage;       // slots freed by relocation
   uint32_t max_label;     // load: largest vertex label
-  uint32_t pad2;
+  uint32_t hub_top;       // hub hash slots allocated
 };
+
+// DFS scheduling counters, one per 128-byte line (reset before every DFS launch)
+#define GM_SCHED_TICKET 0   // tickets taken by warps waiting for donated work
+#define GM_SCHED_RESERVE 32 // donated-task slots reserved (slot t goes to ticket t)
+#define GM_SCHED_BUSY 64    // warps holding work, including reserved but unclaimed slots
+#define GM_SCHED_WORDS 128
 
 // ---------------------------------------------------------------------------
 // device view of the dynamic CSR (passed by value)
@@ -50,6 +58,14 @@ struct GraphDev {
   uint32_t *col;         // [pool] adjacency keys
   uint32_t *etag;        // [pool] batch tag of flagged entries
   uint8_t *nlf;          // [n * nlfw] per-label neighbour counts of the union graph, saturated at 255
+  // hub index: vertices whose list had >= GM_HUB_MIN entries at load keep the
+  // start of every label segment and an open-addressing hash set of their keys
+  const int32_t *hub_id; // [n] hub number or -1
+  uint32_t *hub_lofs;    // [nhub * (nlab + 1)] label-segment starts within the list
+  uint2 *hub_tab;        // [nhub] {first slot in hub_keys, log2 capacity} (capacity 0: no table)
+  uint32_t *hub_keys;    // hash slots (GM_EMPTY or an adjacency key)
+  uint32_t hub_keys_cap;
+  int32_t nhub;
   int32_t n;
   int32_t idb;           // id bits
   int32_t nlab;          // labels 0..nlab-1
@@ -85,6 +101,21 @@ struct WorkItem {
   uint32_t len;  // slots in the slice
 };
 
+// Work split off by a busy DFS warp for an idle one: the slots [lo, lo+len)
+// of the driver segment of one partial match at stored level `depth` (its
+// vertices at positions 2..depth+2 in m[]; positions 0, 1 are the update's
+// endpoints), or, with depth -1, a slice of a seed's level-2 segment.
+#define GM_TASK_M 12
+struct Task {
+  uint32_t upd;
+  uint16_t plan;
+  int8_t depth;
+  uint8_t drv;
+  uint32_t lo;
+  uint32_t len;
+  uint32_t m[GM_TASK_M];
+};
+
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
@@ -101,6 +132,13 @@ __device__ __forceinline__ uint32_t gm_lower_bound(const uint32_t *__restrict__ 
     if (__ldg(a + mid) < key) lo = mid + 1; else hi = mid;
   }
   return lo;
+}
+
+__host__ __device__ __forceinline__ uint32_t gm_hash(uint32_t k) {
+  k ^= k >> 16; k *= 0x85ebca6bu;
+  k ^= k >> 13; k *= 0xc2b2ae35u;
+  k ^= k >> 16;
+  return k;
 }
 
 __device__ __forceinline__ void gm_set_err(GmStatus *st, int code) {

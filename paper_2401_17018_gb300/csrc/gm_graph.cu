@@ -121,6 +121,63 @@ __global__ void k_nlf(GraphDev g, const uint32_t *__restrict__ verts, const uint
   }
 }
 
+// hub index rebuild: one warp per listed vertex that is a hub.  Label-segment
+// starts come from lower bounds (lane l -> label l); the hash set is cleared
+// and refilled from the list, moving to a larger slot range (from the hub
+// pool) when the list outgrew half of the table; if the pool is exhausted the
+// vertex keeps no table and lookups fall back to binary search.
+__global__ void k_hub(GraphDev g, const uint32_t *__restrict__ verts, const uint32_t *__restrict__ nverts_dev,
+                      uint32_t nverts, GmStatus *st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t nv = nverts_dev ? *nverts_dev : nverts;
+  const int s = g.idb + 1;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nv; w += nw) {
+    const uint32_t v = verts ? verts[w] : (uint32_t)w;
+    const int32_t h = g.hub_id[v];
+    if (h < 0) continue;
+    const uint2 a = g.adj[v];
+    const uint32_t *L = g.col + a.x;
+    uint32_t *lofs = g.hub_lofs + (size_t)h * (g.nlab + 1);
+    for (int l0 = 0; l0 <= g.nlab; l0 += 32) {
+      int l = l0 + lane;
+      if (l <= g.nlab) lofs[l] = (l >= g.nlab) ? a.y : lb_coherent(L, a.y, (uint32_t)l << s);
+    }
+    if (g.hub_keys == nullptr) continue;
+    uint2 t = g.hub_tab[h];
+    uint32_t cap = t.y ? (1u << t.y) : 0u;
+    if (2ull * a.y + 2 > cap) {
+      uint32_t bits = 3;
+      while ((1ull << bits) < 3ull * a.y + 8) bits++;
+      uint32_t off = 0;
+      int ok = 0;
+      if (lane == 0) {
+        off = atomicAdd(&st->hub_top, 1u << bits);
+        ok = (uint64_t)off + (1ull << bits) <= g.hub_keys_cap;
+      }
+      off = __shfl_sync(GM_FULL, off, 0);
+      ok = __shfl_sync(GM_FULL, ok, 0);
+      t = ok ? make_uint2(off, bits) : make_uint2(0, 0);
+      if (lane == 0) g.hub_tab[h] = t;
+      cap = t.y ? (1u << t.y) : 0u;
+    }
+    if (!cap) continue;
+    uint32_t *T = g.hub_keys + t.x;
+    for (uint32_t i = lane; i < cap; i += 32) T[i] = GM_EMPTY;
+    __syncwarp();
+    const uint32_t mask = cap - 1;
+    for (uint32_t i = lane; i < a.y; i += 32) {
+      const uint32_t key = L[i];
+      uint32_t p = gm_hash(key >> 1) & mask;
+      for (uint32_t probe = 0; probe < cap; probe++) {
+        if (atomicCAS(T + p, GM_EMPTY, key) == GM_EMPTY) break;
+        p = (p + 1) & mask;
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // ------------------------------- stage --------------------------------------
 // sort key: (vertex << 33) | (deletion << 32) | adjacency key with flag set,
 // so a vertex's group lists its insertions (sorted) before its deletions.
@@ -443,6 +500,18 @@ int gm_nlf(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32
   return GAMMA_OK;
 }
 
+int gm_hub(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32_t nverts_max, GmStatus *st,
+           cudaStream_t s) {
+  if (nverts_max == 0 || g.nhub == 0) return GAMMA_OK;
+  int threads = 256;
+  int64_t blocks = ((int64_t)nverts_max * 32 + threads - 1) / threads;
+  if (blocks > 8192) blocks = 8192;
+  k_hub<<<(int)blocks, threads, 0, s>>>(g, verts, nverts_dev, nverts_max, st);
+  GM_LAUNCHED();
+  GM_CUDA(cudaGetLastError());
+  return GAMMA_OK;
+}
+
 int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, int64_t b, StageBufs &sb,
              GmStatus *st, cudaStream_t s) {
   const int64_t n2 = 2 * b;
@@ -472,7 +541,9 @@ int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *ds
   k_stage_merge<<<(int)mb, 256, 0, s>>>(g, sb.keys, sb.vals, n2, sb.gv, sb.gstart, sb.gins, sb.greloc, sb.bkeys, st);
   GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
-  return gm_nlf(g, sb.gv, &st->ntouched, (uint32_t)n2, s);
+  rc = gm_nlf(g, sb.gv, &st->ntouched, (uint32_t)n2, s);
+  if (rc) return rc;
+  return gm_hub(g, sb.gv, &st->ntouched, (uint32_t)n2, st, s);
 }
 
 int gm_commit(GraphDev g, const StageBufs &sb, int64_t b, GmStatus *st, cudaStream_t s) {
@@ -483,7 +554,9 @@ int gm_commit(GraphDev g, const StageBufs &sb, int64_t b, GmStatus *st, cudaStre
   k_commit<<<(int)mb, 256, 0, s>>>(g, sb.gv, sb.gins, st);
   GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
-  return gm_nlf(g, sb.gv, &st->ntouched, (uint32_t)n2, s);
+  int rc = gm_nlf(g, sb.gv, &st->ntouched, (uint32_t)n2, s);
+  if (rc) return rc;
+  return gm_hub(g, sb.gv, &st->ntouched, (uint32_t)n2, st, s);
 }
 
 int gm_begin_group(GmStatus *st, cudaStream_t s) {

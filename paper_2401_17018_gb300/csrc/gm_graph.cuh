@@ -21,6 +21,8 @@ int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m,
                   uint32_t **etag_out, uint32_t *pool_cap_out, double pool_factor, uint64_t pool_reserve,
                   GmStatus *st, GmStatus *h_st, cudaStream_t s);
 int gm_nlf(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32_t nverts_max, cudaStream_t s);
+int gm_hub(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32_t nverts_max, GmStatus *st,
+           cudaStream_t s);
 int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, int64_t b, StageBufs &sb,
              GmStatus *st, cudaStream_t s);
 int gm_commit(GraphDev g, const StageBufs &sb, int64_t b, GmStatus *st, cudaStream_t s);
@@ -51,6 +53,11 @@ struct MatchArgs {
   int nlev;                    // stored DFS levels (max q - 3, >= 1)
   int warps_per_block;
   int count_bytes;             // accumulate algorithmic bytes into st->alg_bytes
+  Task *tasks;                 // donated work (null: no donation)
+  uint32_t *sched;             // [GM_SCHED_WORDS] scheduling counters
+  uint32_t *task_seq;          // [task_cap] 1 once the task in the slot is written
+  uint32_t task_cap;
+  uint64_t idle_limit_ns;      // longest an idle warp waits for work before flagging an error
   GmStatus *st;
 };
 

@@ -49,10 +49,31 @@ __device__ __forceinline__ uint32_t probe_bytes(uint32_t d) {
 
 __device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t x, uint32_t sdel,
                                         uint32_t upd, uint64_t &bytes) {
+  const uint32_t key = x & ~1u;
+  const int32_t h = __ldg(g.hub_id + w);
+  if (h >= 0) {
+    // hub: probe its hash set; a flagged key still needs the tag from the list
+    const uint2 t = __ldg(g.hub_tab + h);
+    if (t.y) {
+      const uint32_t mask = (1u << t.y) - 1u;
+      const uint32_t *T = g.hub_keys + t.x;
+      uint32_t p = gm_hash(key >> 1) & mask;
+      bytes += 12;
+      for (uint32_t probe = 0; probe <= mask; probe++) {
+        const uint32_t e = __ldg(T + p);
+        bytes += (probe == 0 || (p & 7u) == 0) ? 32 : 0;
+        if (e == GM_EMPTY) return false;
+        if ((e | 1u) == (key | 1u)) {
+          if (!(e & 1u)) return true;
+          break;  // batch edge: fetch its tag below
+        }
+        p = (p + 1) & mask;
+      }
+    }
+  }
   const uint2 a = __ldg(reinterpret_cast<const uint2 *>(g.adj) + w);
   bytes += probe_bytes(a.y);
   const uint32_t *L = g.col + a.x;
-  const uint32_t key = x & ~1u;
   uint32_t p = gm_lower_bound(L, a.y, key);
   if (p >= a.y) return false;
   uint32_t y = __ldg(L + p);
@@ -76,6 +97,43 @@ __device__ __forceinline__ void seg_bounds(const GraphDev &g, const uint32_t *L,
   lo = gm_lower_bound(L, len, (uint32_t)lab << s);
   uint64_t up = (uint64_t)(lab + 1) << s;
   hi = (up >> 32) ? len : gm_lower_bound(L, len, (uint32_t)up);
+}
+
+// absolute col slot and length of N^lab(v): from the hub offset table, else
+// from the prefix of v's per-label counts when none of them is saturated,
+// else by binary search
+__device__ __forceinline__ void label_segment(const GraphDev &g, uint32_t v, int lab, uint32_t &lo,
+                                              uint32_t &len, uint64_t &bytes) {
+  const uint2 a = __ldg(reinterpret_cast<const uint2 *>(g.adj) + v);
+  const int32_t h = __ldg(g.hub_id + v);
+  bytes += 12;
+  if (h >= 0) {
+    const uint32_t *o = g.hub_lofs + (size_t)h * (g.nlab + 1) + lab;
+    const uint32_t s0 = __ldg(o), s1 = __ldg(o + 1);
+    lo = a.x + s0;
+    len = s1 - s0;
+    bytes += 8;
+    return;
+  }
+  const uint8_t *row = g.nlf + (size_t)v * g.nlfw;
+  uint32_t pre = 0, sat = 0;
+  for (int l = 0; l < lab; l++) {
+    const uint32_t c = __ldg(row + l);
+    pre += c;
+    sat |= (c == 255u);
+  }
+  const uint32_t c = __ldg(row + lab);
+  bytes += lab + 1;
+  if (!sat && c < 255u) {
+    lo = a.x + pre;
+    len = c;
+    return;
+  }
+  uint32_t slo, shi;
+  seg_bounds(g, g.col + a.x, a.y, lab, slo, shi);
+  bytes += 2u * probe_bytes(a.y);
+  lo = a.x + slo;
+  len = shi - slo;
 }
 
 // ------------------------------------------------------------------ seeding
@@ -145,13 +203,12 @@ __global__ void k_seed(MatchArgs a) {
         const uint16_t bw = P.bwd[2];
         uint32_t best_len = 0xffffffffu, best_lo = 0;
         int drv = 0;
+        uint64_t nb = 0;
         for (int pos = 0; pos < 2; pos++) {
           if (!((bw >> pos) & 1)) continue;
-          uint32_t w = pos ? v2 : v1;
-          uint2 ad = __ldg(reinterpret_cast<const uint2 *>(g.adj) + w);
-          uint32_t lo, hi;
-          seg_bounds(g, g.col + ad.x, ad.y, lab2, lo, hi);
-          if (hi - lo < best_len) { best_len = hi - lo; best_lo = ad.x + lo; drv = pos; }
+          uint32_t lo, len;
+          label_segment(g, pos ? v2 : v1, lab2, lo, len, nb);
+          if (len < best_len) { best_len = len; best_lo = lo; drv = pos; }
         }
         if (best_len == 0 || best_len == 0xffffffffu) continue;
         uint32_t nit = (best_len + a.grain - 1) / a.grain;
@@ -182,9 +239,10 @@ __global__ void k_seed(MatchArgs a) {
 // ------------------------------------------------------------------ DFS
 struct WarpHdr {
   Plan plan;
-  uint32_t cnt[GM_MAXQ];
-  uint32_t cur[GM_MAXQ];
-  uint32_t tot[GM_MAXQ];
+  uint32_t cnt[GM_MAXQ];   // entries stored per level
+  uint32_t cur[GM_MAXQ];   // expansion pairs consumed per level
+  uint32_t tot[GM_MAXQ];   // expansion pairs this warp still owns per level
+  uint32_t full[GM_MAXQ];  // expansion pairs of the level before any donation
 };
 
 __host__ __device__ inline size_t smem_per_warp(int tile, int nlev) {
@@ -195,6 +253,72 @@ __host__ __device__ inline size_t smem_per_warp(int tile, int nlev) {
   b += lt * 2;                  // PAR
   b += lt;                      // DRV
   return (b + 15) & ~(size_t)15;
+}
+
+constexpr uint32_t DONATE_EVERY = 16;  // expansion steps between looks at the waiting tickets
+constexpr uint32_t DONATE_MIN = 64;    // pairs a level must still own to be split
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int32_t vload(const int32_t *p) { return *(const volatile int32_t *)p; }
+__device__ __forceinline__ uint32_t vload(const uint32_t *p) { return *(const volatile uint32_t *)p; }
+
+// lane 0 of a warp without work: take a ticket and wait (bounded) until the
+// slot with that number is donated, or until no warp holds work any more.
+// Returns true with the slot to run (already counted busy by its donor).
+__device__ bool idle_wait(const MatchArgs &a, uint64_t &slot) {
+  uint32_t *sched = a.sched;
+  const uint32_t t = atomicAdd(sched + GM_SCHED_TICKET, 1u);
+  const uint64_t t0 = global_ns();
+  uint32_t ns = 128;
+  for (uint32_t poll = 0;; poll++) {
+    if (t < vload(sched + GM_SCHED_RESERVE)) {
+      slot = t;
+      return true;
+    }
+    if ((poll & 7u) == 0) {
+      if (vload(&a.st->abort)) return false;
+      if (vload(sched + GM_SCHED_BUSY) == 0u) {
+        __threadfence();
+        if (t >= vload(sched + GM_SCHED_RESERVE)) return false;
+        continue;
+      }
+      if (global_ns() - t0 > a.idle_limit_ns) {  // nothing arrived for too long: report, do not hang
+        gm_set_err(a.st, GAMMA_ETIMEOUT);
+        atomicExch(&a.st->abort, 1);
+        return false;
+      }
+    }
+    __nanosleep(ns);
+    if (ns < 4096) ns <<= 1;
+  }
+}
+
+// lane 0 of a busy warp: reserve n consecutive task slots (never past the
+// capacity) and count their future runners as busy
+__device__ bool reserve_tasks(const MatchArgs &a, uint32_t n, uint32_t &base) {
+  uint32_t *sched = a.sched;
+  atomicAdd(sched + GM_SCHED_BUSY, n);
+  for (int tries = 0; tries < 64; tries++) {
+    uint32_t r = vload(sched + GM_SCHED_RESERVE);
+    if ((uint64_t)r + n > a.task_cap) break;
+    if (atomicCAS(sched + GM_SCHED_RESERVE, r, r + n) == r) { base = r; return true; }
+  }
+  atomicSub(sched + GM_SCHED_BUSY, n);
+  return false;
+}
+
+// tickets waiting for a slot (warp-uniform)
+__device__ __forceinline__ uint32_t demand(const MatchArgs &a) {
+  int32_t d = 0;
+  if ((threadIdx.x & 31) == 0)
+    d = (int32_t)(vload(a.sched + GM_SCHED_TICKET) - vload(a.sched + GM_SCHED_RESERVE));
+  d = __shfl_sync(GM_FULL, d, 0);
+  return d > 0 ? (uint32_t)d : 0u;
 }
 
 __global__ void k_dfs(MatchArgs a) {
@@ -217,32 +341,99 @@ __global__ void k_dfs(MatchArgs a) {
   if (warp_read(&st->err)) return;
   const uint64_t nitems = min(*(volatile uint64_t *)&st->nitems, a.item_cap);
   int cur_plan = -1;
+  bool items_done = false;
 
   while (true) {
-    uint64_t it = 0;
-    if (lane == 0) it = atomicAdd((unsigned long long *)&st->next_item, 1ull);
-    it = __shfl_sync(GM_FULL, it, 0);
-    if (it >= nitems) break;
-    if (warp_read(&st->abort)) break;
-    const WorkItem w = a.items[it];
-    if ((int)w.plan != cur_plan) {
-      const uint32_t *src = reinterpret_cast<const uint32_t *>(a.plans + w.plan);
+    // ---------------- acquire work: a seed item, else a donated task, else wait
+    int kind = 0;  // 1 item, 2 task, 0 finished
+    uint64_t slot = 0;
+    if (lane == 0) {
+      atomicAdd(a.sched + GM_SCHED_BUSY, 1u);
+      if (!items_done && !vload(&st->abort)) {
+        uint64_t it = atomicAdd((unsigned long long *)&st->next_item, 1ull);
+        if (it < nitems) { kind = 1; slot = it; } else items_done = true;
+      }
+      if (!kind) {
+        atomicSub(a.sched + GM_SCHED_BUSY, 1u);
+        if (a.tasks && idle_wait(a, slot)) kind = 2;
+      }
+      if (kind == 2) {  // the donor publishes right after reserving; wait for it (bounded)
+        const uint64_t t0 = global_ns();
+        while (vload(&a.task_seq[slot]) != 1u) {
+          if (global_ns() - t0 > 1000000000ull) {
+            gm_set_err(st, GAMMA_ETIMEOUT);
+            atomicExch(&st->abort, 1);
+            atomicSub(a.sched + GM_SCHED_BUSY, 1u);
+            kind = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+        __threadfence();
+      }
+    }
+    kind = __shfl_sync(GM_FULL, kind, 0);
+    if (!kind) break;
+    slot = __shfl_sync(GM_FULL, slot, 0);
+
+    // ---------------- the unit of work as (update, plan, depth, drv, lo, len, m[])
+    uint32_t word = 0;  // lane j holds word j of the task record
+    if (kind == 1) {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(a.items + slot);
+      if (lane < 4) word = src[lane];
+      // WorkItem {upd, plan|drv<<16|pad<<24, lo, len} -> task words {upd, plan|depth|drv, lo, len}
+      if (lane == 1) word = (word & 0xffffu) | (0xffu << 16) | (((word >> 16) & 0xffu) << 24);
+    } else {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(a.tasks + slot);
+      if (lane < 16) word = __ldcg(src + lane);
+    }
+    const uint32_t upd = __shfl_sync(GM_FULL, word, 0);
+    const uint32_t w1 = __shfl_sync(GM_FULL, word, 1);
+    const uint32_t wlo = __shfl_sync(GM_FULL, word, 2);
+    const uint32_t wlen = __shfl_sync(GM_FULL, word, 3);
+    const int plan = (int)(w1 & 0xffffu);
+    const int depth = (int)(int8_t)((w1 >> 16) & 0xffu);
+    const uint32_t wdrv = (w1 >> 24) & 0xffu;
+    const uint32_t mword = __shfl_sync(GM_FULL, word, (lane + 4) & 31);  // m[lane]
+
+    if (plan != cur_plan) {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(a.plans + plan);
       uint32_t *dst = reinterpret_cast<uint32_t *>(&H->plan);
       for (int i = lane; i < (int)(sizeof(Plan) / 4); i += 32) dst[i] = __ldg(src + i);
-      cur_plan = w.plan;
+      cur_plan = plan;
     }
     if (lane < GM_MAXQ) H->cnt[lane] = 0;
     __syncwarp();
+    int lev;
+    uint32_t root_lo = wlo, root_len = wlen, root_cur = 0, root_drv = wdrv;
+    if (depth >= 0) {
+      // levels 0..depth hold the donated partial match; only level `depth` has pairs left
+      if (lane <= depth) {
+        H->cnt[lane] = 1;
+        V[lane * T] = mword;
+        PAR[lane * T] = 0;
+        H->cur[lane] = 0;
+        H->tot[lane] = (lane == depth) ? wlen : 0u;
+        H->full[lane] = H->tot[lane];
+      }
+      if (lane == depth) {
+        LO[depth * T] = wlo;
+        EX[depth * T] = 0;
+        DRV[depth * T] = (uint8_t)wdrv;
+      }
+      __syncwarp();
+      lev = depth;
+      root_len = 0;
+    } else {
+      lev = -1;
+    }
     const Plan &P = H->plan;
     const int q = P.q, last = q - 1;
-    const uint32_t upd = w.upd;
     const uint32_t m0 = __ldg(a.cu + upd), m1 = __ldg(a.cv + upd);
     const uint32_t sdel = a.op[upd] < 0 ? 1u : 0u;
     uint64_t wcount = 0;
     uint64_t lbytes = 0;  // this lane's algorithmic bytes (only reported with count_bytes)
     uint32_t chunks = 0;
-    int lev = -1;            // parent level (-1 = the seed itself)
-    uint32_t root_cur = 0;
 
     // prepare level L (position L+2): driver segment of every entry for position L+3
     auto prepare = [&](int L) {
@@ -256,8 +447,7 @@ __global__ void k_dfs(MatchArgs a) {
         uint32_t len = 0, lo = 0;
         int drv = 0;
         if (i < n) {
-          // walk the chain of entry i, keep the backward neighbour with the
-          // smallest label-lab count (driver choice only; exact bounds below)
+          // the backward neighbour with the fewest label-lab neighbours drives
           uint32_t best = 0xffffffffu, bestv = 0;
           uint32_t e = i;
           for (int l2 = L; l2 >= 0; l2--) {
@@ -278,14 +468,7 @@ __global__ void k_dfs(MatchArgs a) {
             if (c < best) { best = c; bestv = m0; drv = 0; }
           }
           lbytes += 4u * __popc(bw);
-          if (best > 0) {
-            uint2 ad = __ldg(reinterpret_cast<const uint2 *>(g.adj) + bestv);
-            uint32_t slo, shi;
-            seg_bounds(g, g.col + ad.x, ad.y, lab, slo, shi);
-            lbytes += 2u * probe_bytes(ad.y);
-            lo = ad.x + slo;
-            len = shi - slo;
-          }
+          if (best > 0) label_segment(g, bestv, lab, lo, len, lbytes);
           LO[L * T + i] = lo;
           DRV[L * T + i] = (uint8_t)drv;
         }
@@ -297,14 +480,83 @@ __global__ void k_dfs(MatchArgs a) {
         if (i < n) EX[L * T + i] = carry + inc - len;
         carry += __shfl_sync(GM_FULL, inc, 31);
       }
-      if (lane == 0) { H->tot[L] = carry; H->cur[L] = 0; }
+      if (lane == 0) { H->tot[L] = carry; H->full[L] = carry; H->cur[L] = 0; }
+      __syncwarp();
+    };
+
+    // split off the second half of the shallowest level that still owns
+    // enough pairs and publish it as tasks for idle warps
+    auto donate = [&](uint32_t want) {
+      int L = -2;
+      if (root_len > root_cur && root_len - root_cur >= DONATE_MIN) L = -1;
+      for (int l = 0; L == -2 && l <= lev; l++)
+        if (H->tot[l] > H->cur[l] && H->tot[l] - H->cur[l] >= DONATE_MIN && l < GM_TASK_M) L = l;
+      if (L == -2) return;
+      const uint32_t c0 = (L < 0) ? root_cur : H->cur[L];
+      const uint32_t t0 = (L < 0) ? root_len : H->tot[L];
+      const uint32_t s = c0 + max(32u, ((t0 - c0) / 2) & ~31u);
+      if (s >= t0) return;
+      if (L < 0) {
+        uint32_t base = 0;
+        int ok = 0;
+        if (lane == 0 && reserve_tasks(a, 1, base)) {
+          Task *t = a.tasks + base;
+          t->upd = upd; t->plan = (uint16_t)plan; t->depth = -1; t->drv = (uint8_t)root_drv;
+          t->lo = root_lo + s; t->len = t0 - s;
+          __threadfence();
+          *(volatile uint32_t *)&a.task_seq[base] = 1u;
+          ok = 1;
+        }
+        if (__shfl_sync(GM_FULL, ok, 0)) root_len = s;
+        return;
+      }
+      // entries covering [s, t0): donate at most 32 of them, always the tail
+      const uint32_t n = H->cnt[L];
+      const uint32_t *ex = EX + L * T;
+      auto entry_of = [&](uint32_t x) {  // last entry with ex <= x
+        uint32_t lo = 0, hi = n;
+        while (hi - lo > 1) {
+          uint32_t mid = (lo + hi) >> 1;
+          if (ex[mid] <= x) lo = mid; else hi = mid;
+        }
+        return lo;
+      };
+      const uint32_t e_s = entry_of(s), e_end = entry_of(t0 - 1);
+      const uint32_t most = min(32u, max(want, 1u));
+      const uint32_t e_first = (e_end - e_s >= most) ? e_end - (most - 1) : e_s;
+      const uint32_t s2 = (e_first == e_s) ? s : ex[e_first];
+      const uint32_t nt = e_end - e_first + 1;
+      uint32_t base = 0;
+      int ok = 0;
+      if (lane == 0) ok = reserve_tasks(a, nt, base) ? 1 : 0;
+      ok = __shfl_sync(GM_FULL, ok, 0);
+      if (!ok) return;
+      base = __shfl_sync(GM_FULL, base, 0);
+      if ((uint32_t)lane < nt) {
+        const uint32_t e = e_first + lane;
+        const uint32_t elen = ((e + 1 < n) ? ex[e + 1] : H->full[L]) - ex[e];
+        const uint32_t a0 = max(s2, ex[e]), a1 = min(t0, ex[e] + elen);
+        Task *t = a.tasks + base + lane;
+        t->upd = upd; t->plan = (uint16_t)plan; t->depth = (int8_t)L; t->drv = DRV[L * T + e];
+        t->lo = LO[L * T + e] + (a0 - ex[e]);
+        t->len = a1 - a0;
+        uint32_t ee = e;
+        for (int l2 = L; l2 >= 0; l2--) {
+          t->m[l2] = V[l2 * T + ee];
+          ee = PAR[l2 * T + ee];
+        }
+        __threadfence();
+        *(volatile uint32_t *)&a.task_seq[base + lane] = 1u;
+      }
+      __syncwarp();
+      if (lane == 0) H->tot[L] = s2;
       __syncwarp();
     };
 
     while (true) {
       const int c = lev + 3;  // position of the candidates produced from level lev
       uint32_t total, cur;
-      if (lev < 0) { total = w.len; cur = root_cur; }
+      if (lev < 0) { total = root_len; cur = root_cur; }
       else { total = H->tot[lev]; cur = H->cur[lev]; }
       if (cur >= total) {
         if (lev < 0) break;
@@ -323,11 +575,11 @@ __global__ void k_dfs(MatchArgs a) {
       // ---- one 32-wide expansion step
       const uint32_t gidx = cur + lane;
       bool ok = gidx < total;
-      uint32_t e = 0, slot = 0;
+      uint32_t e = 0, slot2 = 0;
       int drv;
       if (lev < 0) {
-        slot = w.lo + gidx;
-        drv = w.drv;
+        slot2 = root_lo + gidx;
+        drv = root_drv;
       } else {
         const uint32_t n = H->cnt[lev];
         const uint32_t *ex = EX + lev * T;
@@ -337,13 +589,13 @@ __global__ void k_dfs(MatchArgs a) {
           if (ex[mid] <= gidx) lo = mid; else hi = mid;
         }
         e = lo;
-        slot = LO[lev * T + e] + (gidx - ex[e]);
+        slot2 = LO[lev * T + e] + (gidx - ex[e]);
         drv = DRV[lev * T + e];
       }
       chunks++;
-      uint32_t x = ok ? __ldg(g.col + slot) : 0u;
+      uint32_t x = ok ? __ldg(g.col + slot2) : 0u;
       const uint32_t id = (x >> 1) & g.idmask;
-      if (ok && (x & 1u)) ok = tag_ok(__ldg(g.etag + slot), sdel, upd);
+      if (ok && (x & 1u)) ok = tag_ok(__ldg(g.etag + slot2), sdel, upd);
       const uint16_t chk_edge = P.bwd[c] & (uint16_t)~(1u << drv);
       const uint16_t chk_neq = P.samelab[c];
       if (ok && (chk_edge | chk_neq)) {
@@ -404,10 +656,14 @@ __global__ void k_dfs(MatchArgs a) {
         prepare(lev + 1);
         lev++;
       }
+      if (a.tasks && (chunks % DONATE_EVERY) == 0) {
+        const uint32_t want = demand(a);
+        if (want) donate(want);
+      }
       if ((chunks & 1023u) == 0 && warp_read(&st->abort)) break;
     }
     if (a.count_bytes) {
-      lbytes += (lane == 0) ? sizeof(WorkItem) : 0;
+      lbytes += (lane == 0) ? 16u : 0u;
       for (int d = 16; d > 0; d >>= 1) lbytes += __shfl_down_sync(GM_FULL, lbytes, d);
       if (lane == 0) atomicAdd((unsigned long long *)&st->alg_bytes, (unsigned long long)lbytes);
     }
@@ -422,6 +678,8 @@ __global__ void k_dfs(MatchArgs a) {
         atomicExch(&st->abort, 1);
         gm_set_err(st, GAMMA_ETIMEOUT);
       }
+      __threadfence();
+      atomicSub(a.sched + GM_SCHED_BUSY, 1u);
     }
     __syncwarp();
   }
@@ -453,6 +711,7 @@ int gm_dfs(const MatchArgs &a, int num_sms, cudaStream_t s) {
   int per_sm = 0;
   GM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfs, wpb * 32, smem));
   if (per_sm < 1) return GAMMA_EINVAL;
+  GM_CUDA(cudaMemsetAsync(a.sched, 0, GM_SCHED_WORDS * sizeof(uint32_t), s));
   k_dfs<<<num_sms * per_sm, wpb * 32, smem, s>>>(a);
   GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());

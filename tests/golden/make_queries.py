@@ -34,8 +34,8 @@ SPECS = {
     "batched": ("mid", 90_000, 10_000,
                 [("sparse" if i % 2 == 0 else "dense", 4 + (i * 7) % 9) for i in range(64)]),
 }
-STRIDE = 100
-BUDGET = 3_000_000
+STRIDE = 200
+BUDGET = 10_000_000
 
 _W = None
 

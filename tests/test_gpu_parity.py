@@ -31,7 +31,7 @@ def gpu_run(G, graph, queries, batch, flags=0, rows=True, **opts):
         ctx.load_graph(graph.n, graph.labels, graph.src, graph.dst)
         qids = [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
         if rows:
-            pos, neg, r, req = ctx.apply_batch(batch.op, batch.src, batch.dst, qids, row_capacity=1 << 20)
+            pos, neg, r, req = ctx.apply_batch(batch.op, batch.src, batch.dst, qids, row_capacity=1 << 22)
             assert req == len(r)
         else:
             pos, neg = ctx.apply_batch(batch.op, batch.src, batch.dst, qids)
@@ -113,7 +113,7 @@ def test_tiny_workload_mixed_many_queries(G):
     att = 0
     while len(qs) < 12:
         kind = ["dense", "sparse", "tree"][att % 3]
-        q = I.random_walk_query(off, nbr, g.labels, 4 + att % 3, kind, 5, att)
+        q = I.random_walk_query(off, nbr, g.labels, 4 + att % 2, kind, 5, att)
         att += 1
         if q is not None:
             qs.append(q)
