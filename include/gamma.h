@@ -57,6 +57,8 @@ extern "C" {
 #define GAMMA_F_PER_QUERY 0x4u   /* plain form: one seed+DFS launch sequence per query */
 #define GAMMA_F_GRAPH 0x8u       /* replay the match phase as a captured CUDA graph */
 #define GAMMA_F_COUNT_BYTES 0x10u /* count the DFS kernel's algorithmic bytes (gamma_stats.alg_bytes) */
+#define GAMMA_F_NO_LEAF 0x20u   /* always enumerate a last query vertex that has one earlier neighbour
+                                   (default: count it in closed form when no rows are requested) */
 
 typedef struct gamma_ctx gamma_ctx;
 
@@ -96,6 +98,7 @@ typedef struct {
   uint64_t expansions; /* 32-candidate expansion steps of the last apply */
   uint64_t alg_bytes;  /* DFS algorithmic bytes of the last apply (GAMMA_F_COUNT_BYTES) */
   uint64_t kernel_launches; /* kernels the library has launched in this process so far */
+  int64_t graph_captures;   /* CUDA graphs captured by this context (GAMMA_F_GRAPH) */
 } gamma_stats;
 
 /* Create a context on options->device (options may be NULL: defaults).
@@ -139,6 +142,19 @@ GAMMA_API int gamma_apply_batch(gamma_ctx *ctx, int64_t b, const int8_t *op,
                       uint64_t *out_pos, uint64_t *out_neg,
                       gamma_matches *opt_out);
 
+/* Several update requests staged as one batch (continuous batching): request
+ * r is updates [req_off[r], req_off[r+1]) of the arrays (req_off[0] = 0,
+ * host array of nreq + 1 offsets).  The result is the same as applying the
+ * requests one after another (apply + commit each): request r sees the graph
+ * after requests 0..r-1, and its counts, out_pos[r*nq + j] / out_neg[r*nq + j]
+ * for query qids[j], are its own incremental matches.  The requests must touch
+ * pairwise disjoint edges (else GAMMA_EINVAL, graph unchanged).  Afterwards
+ * the batch is staged as with gamma_apply_batch; gamma_commit applies all of
+ * it.  No match rows. */
+GAMMA_API int gamma_apply_batches(gamma_ctx *ctx, int32_t nreq, const int64_t *req_off, const int8_t *op,
+                                  const int32_t *src, const int32_t *dst, int32_t nq, const int32_t *qids,
+                                  uint64_t *out_pos, uint64_t *out_neg);
+
 /* Re-run the matching of the staged batch and write its match rows into out
  * (after GAMMA_EOVERFLOW, with a larger buffer).  GAMMA_ESTATE if no batch is
  * staged. */
@@ -168,6 +184,53 @@ GAMMA_API int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out);
 /* Change flags / tuning knobs between batches (fields as in gamma_options;
  * 0 keeps the current value for the three tuning fields). */
 GAMMA_API int gamma_set_options(gamma_ctx *ctx, const gamma_options *options);
+
+/* ------------------------------------------------------------------------
+ * Served form: a worker thread applies a stream of update requests to the
+ * device-resident graph, in arrival order.  Requests that arrive while the
+ * GPU is busy wait; when it is free the worker stages every waiting request
+ * it can admit together (gamma_apply_batches: continuous batching, each
+ * request still gets exactly its own result) and commits them.  A group
+ * stops at the first request that touches an edge already in the group, at
+ * max_requests / max_updates, or when its estimated device memory would
+ * exceed hbm_fraction of the free HBM (admission).  While a server runs, its
+ * context belongs to the worker thread: call nothing else on it.
+ * ------------------------------------------------------------------------ */
+typedef struct gamma_server gamma_server;
+
+typedef struct {
+  int64_t max_updates;   /* updates staged together at most (0 = 2^21) */
+  int32_t max_requests;  /* requests staged together at most (0 = 256) */
+  double hbm_fraction;   /* admit while the estimate <= this share of free HBM (0 = 0.5) */
+} gamma_server_options;
+
+typedef struct {
+  double arrival_ms;   /* submit time (ms since the server started) */
+  double start_ms;     /* its group was handed to the GPU */
+  double done_ms;      /* its group was committed and counts were on the host */
+  int32_t group_size;  /* requests staged together with it (itself included) */
+  int32_t status;      /* GAMMA_* of its group */
+} gamma_request_info;
+
+typedef struct {
+  int64_t groups, requests, updates, max_group;
+  double busy_ms;      /* worker time spent in apply + commit */
+} gamma_server_stats;
+
+/* Start serving ctx for the nq queries qids (counts are per query). */
+GAMMA_API int gamma_server_start(gamma_ctx *ctx, int32_t nq, const int32_t *qids,
+                                 const gamma_server_options *options, gamma_server **out);
+/* Queue one request of b updates (host arrays, copied before returning; same
+ * rules as gamma_apply_batch).  *ticket identifies it.  Thread-safe. */
+GAMMA_API int gamma_server_submit(gamma_server *s, int64_t b, const int8_t *op, const int32_t *src,
+                                  const int32_t *dst, int64_t *ticket);
+/* Block until the request is done; out_pos/out_neg (host, nq each) receive its
+ * counts, info its times.  Returns its status; each ticket is waited once. */
+GAMMA_API int gamma_server_wait(gamma_server *s, int64_t ticket, uint64_t *out_pos, uint64_t *out_neg,
+                                gamma_request_info *info);
+GAMMA_API int gamma_server_stats_get(gamma_server *s, gamma_server_stats *out);
+/* Finish the queued requests, stop the worker and free the server. */
+GAMMA_API int gamma_server_stop(gamma_server *s);
 
 /* Message for the last error on ctx (never NULL; "" when none). */
 GAMMA_API const char *gamma_last_error(gamma_ctx *ctx);

@@ -70,6 +70,7 @@ struct gamma_ctx {
   uint2 *d_adj = nullptr;
   uint32_t *d_cap = nullptr, *d_col = nullptr, *d_etag = nullptr;
   uint8_t *d_nlf = nullptr;
+  int32_t *d_vgroup = nullptr;
   int32_t *d_hub_id = nullptr;
   uint32_t *d_hub_lofs = nullptr;
   uint2 *d_hub_tab = nullptr;
@@ -119,7 +120,15 @@ struct gamma_ctx {
   uint32_t *d_task_seq = nullptr;
   int64_t task_seq_cap = 0;
 
+  uint32_t *d_req = nullptr;      // request of each update (several requests staged together)
+  int64_t req_cap = 0;
+  int nreq = 1;
+  cudaGraphExec_t gexec = nullptr;  // last captured apply (GAMMA_F_GRAPH)
+  std::vector<int64_t> gkey;
+  int64_t graph_captures = 0;
+
   GmStatus *d_st = nullptr;
+  GmStatus *h_st_init = nullptr;  // pinned: status at the start of an apply
   GmStatus *h_st = nullptr;       // pinned
   uint64_t *h_cnt = nullptr;      // pinned
   int64_t h_cnt_cap = 0;
@@ -129,6 +138,7 @@ struct gamma_ctx {
   GraphDev gd() const {
     GraphDev g;
     g.label = d_label; g.adj = d_adj; g.cap = d_cap; g.col = d_col; g.etag = d_etag; g.nlf = d_nlf;
+    g.vgroup = d_vgroup;
     g.hub_id = d_hub_id; g.hub_lofs = d_hub_lofs; g.hub_tab = d_hub_tab; g.hub_keys = d_hub_keys;
     g.hub_keys_cap = hub_keys_cap; g.nhub = nhub;
     g.n = n; g.idb = idb; g.nlab = nlab; g.nlfw = nlfw;
@@ -165,6 +175,8 @@ void free_graph(gamma_ctx *ctx) {
   cudaFree(ctx->d_label); cudaFree(ctx->d_adj); cudaFree(ctx->d_cap);
   cudaFree(ctx->d_col); cudaFree(ctx->d_etag); cudaFree(ctx->d_nlf);
   cudaFree(ctx->d_hub_id); cudaFree(ctx->d_hub_lofs); cudaFree(ctx->d_hub_tab); cudaFree(ctx->d_hub_keys);
+  cudaFree(ctx->d_vgroup);
+  ctx->d_vgroup = nullptr;
   ctx->d_label = nullptr; ctx->d_adj = nullptr; ctx->d_cap = nullptr;
   ctx->d_col = nullptr; ctx->d_etag = nullptr; ctx->d_nlf = nullptr;
   ctx->d_hub_id = nullptr; ctx->d_hub_lofs = nullptr; ctx->d_hub_tab = nullptr; ctx->d_hub_keys = nullptr;
@@ -317,10 +329,11 @@ int grow_pool(gamma_ctx *ctx, uint64_t need) {
 }
 
 void reset_status_host(gamma_ctx *ctx) {
-  memset(ctx->h_st, 0, sizeof(GmStatus));
-  ctx->h_st->bad_index = INT64_MAX;
-  ctx->h_st->pool_top = (uint32_t)ctx->pool_top;
-  ctx->h_st->hub_top = (uint32_t)ctx->hub_top;
+  GmStatus *t = ctx->h_st_init;
+  memset(t, 0, sizeof(GmStatus));
+  t->bad_index = INT64_MAX;
+  t->pool_top = (uint32_t)ctx->pool_top;
+  t->hub_top = (uint32_t)ctx->hub_top;
 }
 
 float ev_ms(cudaEvent_t a, cudaEvent_t b) {
@@ -329,19 +342,42 @@ float ev_ms(cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
-// seed + DFS for the staged batch; rows may be null.  Leaves counts in
-// ctx->h_cnt and the status in ctx->h_st.
-int run_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_stride) {
+// device buffers for a batch of b updates, nreq requests and the requested queries
+int prepare_buffers(gamma_ctx *ctx, int64_t b) {
+  StageBufs &sb = ctx->sb;
+  if (b > sb.cap) {
+    int64_t c = std::max<int64_t>(b, 1024);
+    void *ps[] = {sb.cu, sb.cv, sb.cop, sb.keys, sb.tk, sb.vals, sb.tv, sb.head, sb.gid, sb.gv, sb.gstart,
+                  sb.gins, sb.greloc, sb.bkeys};
+    for (void *p : ps) if (p) cudaFree(p);
+    sb = StageBufs();
+    CKC(cudaMalloc((void **)&sb.cu, 4 * c)); CKC(cudaMalloc((void **)&sb.cv, 4 * c));
+    CKC(cudaMalloc((void **)&sb.cop, c));
+    CKC(cudaMalloc((void **)&sb.keys, 16 * c)); CKC(cudaMalloc((void **)&sb.tk, 16 * c));
+    CKC(cudaMalloc((void **)&sb.vals, 8 * c)); CKC(cudaMalloc((void **)&sb.tv, 8 * c));
+    CKC(cudaMalloc((void **)&sb.head, 8 * c)); CKC(cudaMalloc((void **)&sb.gid, 8 * c));
+    CKC(cudaMalloc((void **)&sb.gv, 8 * c)); CKC(cudaMalloc((void **)&sb.gstart, 8 * c));
+    CKC(cudaMalloc((void **)&sb.gins, 8 * c)); CKC(cudaMalloc((void **)&sb.greloc, 8 * c));
+    CKC(cudaMalloc((void **)&sb.bkeys, 8 * c));
+    sb.cap = c;
+  }
+  if (b > ctx->in_cap) {
+    cudaFree(ctx->d_in_op); cudaFree(ctx->d_in_src); cudaFree(ctx->d_in_dst);
+    ctx->d_in_op = nullptr; ctx->d_in_src = nullptr; ctx->d_in_dst = nullptr;
+    int64_t c = std::max<int64_t>(b, 1024);
+    CKC(cudaMalloc((void **)&ctx->d_in_op, c));
+    CKC(cudaMalloc((void **)&ctx->d_in_src, 4 * c));
+    CKC(cudaMalloc((void **)&ctx->d_in_dst, 4 * c));
+    ctx->in_cap = c;
+  }
   const int nq = (int)ctx->qids.size();
-  const int64_t b = ctx->b;
-  const bool per_query = (ctx->flags & GAMMA_F_PER_QUERY) != 0;
-  CK(build_tables(ctx, ctx->qids, per_query));
-  CK(ensure(ctx->d_cnt, ctx->cnt_cap, (int64_t)2 * std::max(nq, 1)));
+  const int64_t ncnt = (int64_t)2 * std::max(nq, 1) * ctx->nreq;
+  CK(ensure(ctx->d_cnt, ctx->cnt_cap, ncnt));
   if (ctx->flags & GAMMA_F_PER_UPDATE) CK(ensure(ctx->d_per_upd, ctx->per_upd_cap, std::max<int64_t>((int64_t)nq * b, 1)));
-  if (ctx->h_cnt_cap < 2 * std::max(nq, 1)) {
+  if (ctx->h_cnt_cap < ncnt) {
     if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
-    CKC(cudaMallocHost((void **)&ctx->h_cnt, sizeof(uint64_t) * 2 * std::max(nq, 1)));
-    ctx->h_cnt_cap = 2 * std::max(nq, 1);
+    CKC(cudaMallocHost((void **)&ctx->h_cnt, sizeof(uint64_t) * ncnt));
+    ctx->h_cnt_cap = ncnt;
   }
   if (ctx->items_cap == 0) CK(ensure(ctx->d_items, ctx->items_cap, std::max<int64_t>(1 << 20, 8 * b)));
   if (ctx->tasks_cap == 0) {
@@ -349,73 +385,133 @@ int run_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_strid
     CK(ensure(ctx->d_task_seq, ctx->task_seq_cap, ctx->tasks_cap));
     CK(ensure(ctx->d_sched, ctx->sched_cap, GM_SCHED_WORDS));
   }
+  if (ctx->nreq > 1) CK(ensure(ctx->d_req, ctx->req_cap, std::max<int64_t>(b, 1)));
+  return build_tables(ctx, ctx->qids, (ctx->flags & GAMMA_F_PER_QUERY) != 0);
+}
+
+// status reset + stage (A1); no host sync
+int enqueue_stage(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const int32_t *ddst) {
+  cudaStream_t s = ctx->stream;
+  CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st_init, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
+  CKC(cudaEventRecord(ctx->ev[0], s));
+  if (ctx->b > 0) CK(gm_stage(ctx->gd(), dop, dsrc, ddst, ctx->b, ctx->sb, ctx->d_st, s));
+  CKC(cudaEventRecord(ctx->ev[1], s));
+  return GAMMA_OK;
+}
+
+// seed (A2) + DFS (A5, A6) for the staged batch, then counts and status to
+// the host; no host sync.  The kernels do nothing once an error is flagged.
+int enqueue_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_stride, bool clear_err) {
+  const int nq = (int)ctx->qids.size();
+  const int64_t b = ctx->b;
+  const bool per_query = (ctx->flags & GAMMA_F_PER_QUERY) != 0;
+  const int64_t ncnt = (int64_t)2 * std::max(nq, 1) * ctx->nreq;
+  cudaStream_t s = ctx->stream;
+  CKC(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(uint64_t) * ncnt, s));
+  if (ctx->flags & GAMMA_F_PER_UPDATE)
+    CKC(cudaMemsetAsync(ctx->d_per_upd, 0, sizeof(uint64_t) * std::max<int64_t>((int64_t)nq * b, 1), s));
+  // clear the match part of the status (abort and nseeds..rows); errors of the stage stay
+  if (clear_err) CKC(cudaMemsetAsync(&ctx->d_st->err, 0, sizeof(int32_t), s));
+  CKC(cudaMemsetAsync(&ctx->d_st->abort, 0, sizeof(int32_t), s));
+  CKC(cudaMemsetAsync(&ctx->d_st->nseeds, 0, 5 * sizeof(uint64_t), s));
+  CKC(cudaMemsetAsync(&ctx->d_st->alg_bytes, 0, sizeof(uint64_t), s));
+  CKC(cudaEventRecord(ctx->ev[2], s));
+  MatchArgs a;
+  a.g = ctx->gd();
+  a.cu = ctx->sb.cu; a.cv = ctx->sb.cv; a.op = ctx->sb.cop; a.b = b;
+  a.grain = ctx->grain;
+  a.items = ctx->d_items; a.item_cap = (uint64_t)ctx->items_cap;
+  a.cnt = ctx->d_cnt;
+  a.req = (ctx->nreq > 1) ? ctx->d_req : nullptr;
+  a.nq = std::max(nq, 1);
+  a.per_upd = (ctx->flags & GAMMA_F_PER_UPDATE) ? ctx->d_per_upd : nullptr;
+  a.use_filter = (ctx->flags & GAMMA_F_NO_FILTER) ? 0 : 1;
+  a.rows = rows_dev; a.row_cap = row_cap; a.row_stride = row_stride;
+  a.budget = ctx->budget;
+  a.tile = ctx->tile;
+  a.warps_per_block = ctx->wpb;
+  a.count_bytes = (ctx->flags & GAMMA_F_COUNT_BYTES) ? 1 : 0;
+  a.leaf = (ctx->flags & GAMMA_F_NO_LEAF) ? 0 : 1;
+  a.bkeys = ctx->sb.keys;
+  a.bvals = ctx->sb.vals;
+  a.gstart = ctx->sb.gstart;
+  a.gins = ctx->sb.gins;
+  a.n2 = (uint32_t)(2 * b);
+  a.tasks = ctx->d_tasks;
+  a.sched = ctx->d_sched;
+  a.task_seq = ctx->d_task_seq;
+  a.task_cap = (uint32_t)ctx->tasks_cap;
+  a.idle_limit_ns = 60ull * 1000000000ull;
+  a.st = ctx->d_st;
+  a.plans = ctx->d_plans; a.nplans = ctx->nplans;
+  a.pair_plans = ctx->d_pair_plans;
+  a.nlev = std::max(1, ctx->maxq - 3);
+  const int np = ctx->nlab * ctx->nlab;
+  const int ngroups = per_query ? nq : 1;
+  bool seeded = false;
+  for (int gi = 0; gi < ngroups; gi++) {
+    if (ctx->group_nplans[gi] == 0) continue;
+    a.pair_off = ctx->d_pair_off + (size_t)gi * (np + 1);
+    if (per_query) CK(gm_begin_group(ctx->d_st, s));
+    CK(gm_seed(a, s));
+    CKC(cudaMemsetAsync(ctx->d_task_seq, 0, sizeof(uint32_t) * ctx->tasks_cap, s));
+    if (!per_query) { CKC(cudaEventRecord(ctx->ev[3], s)); seeded = true; }
+    CK(gm_dfs(a, ctx->num_sms, s));
+  }
+  if (!seeded) CKC(cudaEventRecord(ctx->ev[3], s));
+  CKC(cudaEventRecord(ctx->ev[4], s));
+  CKC(cudaMemcpyAsync(ctx->h_cnt, ctx->d_cnt, sizeof(uint64_t) * ncnt, cudaMemcpyDeviceToHost, s));
+  CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
+  CKC(cudaEventRecord(ctx->ev[5], s));
+  return GAMMA_OK;
+}
+
+void match_stats(gamma_ctx *ctx) {
+  const GmStatus &st = *ctx->h_st;
+  ctx->stats.ms_seed = ev_ms(ctx->ev[2], ctx->ev[3]);
+  ctx->stats.ms_match = ev_ms(ctx->ev[3], ctx->ev[4]);
+  ctx->stats.ms_finalize = ev_ms(ctx->ev[4], ctx->ev[5]);
+  ctx->stats.seeds = (int64_t)st.nseeds;
+  ctx->stats.work_items = (int64_t)st.nitems;
+  ctx->stats.expansions = st.expansions;
+  ctx->stats.alg_bytes = st.alg_bytes;
+}
+
+// the match phase alone, with retries when the work item buffer was too small
+int run_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_stride) {
   for (int attempt = 0; attempt < 4; attempt++) {
-    cudaStream_t s = ctx->stream;
-    CKC(cudaMemsetAsync(ctx->d_cnt, 0, sizeof(uint64_t) * 2 * std::max(nq, 1), s));
-    if (ctx->flags & GAMMA_F_PER_UPDATE)
-      CKC(cudaMemsetAsync(ctx->d_per_upd, 0, sizeof(uint64_t) * std::max<int64_t>((int64_t)nq * b, 1), s));
-    // clear the match part of the status (err/abort and nseeds..rows)
-    CKC(cudaMemsetAsync(&ctx->d_st->err, 0, 2 * sizeof(int32_t), s));
-    CKC(cudaMemsetAsync(&ctx->d_st->nseeds, 0, 5 * sizeof(uint64_t), s));
-    CKC(cudaMemsetAsync(&ctx->d_st->alg_bytes, 0, sizeof(uint64_t), s));
-    CKC(cudaEventRecord(ctx->ev[2], s));
-    MatchArgs a;
-    a.g = ctx->gd();
-    a.cu = ctx->sb.cu; a.cv = ctx->sb.cv; a.op = ctx->sb.cop; a.b = b;
-    a.grain = ctx->grain;
-    a.items = ctx->d_items; a.item_cap = (uint64_t)ctx->items_cap;
-    a.cnt = ctx->d_cnt;
-    a.per_upd = (ctx->flags & GAMMA_F_PER_UPDATE) ? ctx->d_per_upd : nullptr;
-    a.use_filter = (ctx->flags & GAMMA_F_NO_FILTER) ? 0 : 1;
-    a.rows = rows_dev; a.row_cap = row_cap; a.row_stride = row_stride;
-    a.budget = ctx->budget;
-    a.tile = ctx->tile;
-    a.warps_per_block = ctx->wpb;
-    a.count_bytes = (ctx->flags & GAMMA_F_COUNT_BYTES) ? 1 : 0;
-    a.tasks = ctx->d_tasks;
-    a.sched = ctx->d_sched;
-    a.task_seq = ctx->d_task_seq;
-    a.task_cap = (uint32_t)ctx->tasks_cap;
-    a.idle_limit_ns = 60ull * 1000000000ull;
-    a.st = ctx->d_st;
-    a.plans = ctx->d_plans; a.nplans = ctx->nplans;
-    a.pair_plans = ctx->d_pair_plans;
-    a.nlev = std::max(1, ctx->maxq - 3);
-    const int np = ctx->nlab * ctx->nlab;
-    const int ngroups = per_query ? nq : 1;
-    bool seeded = false;
-    for (int gi = 0; gi < ngroups; gi++) {
-      if (ctx->group_nplans[gi] == 0) continue;
-      a.pair_off = ctx->d_pair_off + (size_t)gi * (np + 1);
-      if (per_query) CK(gm_begin_group(ctx->d_st, s));
-      CK(gm_seed(a, s));
-      CKC(cudaMemsetAsync(ctx->d_task_seq, 0, sizeof(uint32_t) * ctx->tasks_cap, s));
-      if (!per_query) { CKC(cudaEventRecord(ctx->ev[3], s)); seeded = true; }
-      CK(gm_dfs(a, ctx->num_sms, s));
-    }
-    if (!seeded) CKC(cudaEventRecord(ctx->ev[3], s));
-    CKC(cudaEventRecord(ctx->ev[4], s));
-    CKC(cudaMemcpyAsync(ctx->h_cnt, ctx->d_cnt, sizeof(uint64_t) * 2 * std::max(nq, 1), cudaMemcpyDeviceToHost, s));
-    CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
-    CKC(cudaEventRecord(ctx->ev[5], s));
-    CKC(cudaStreamSynchronize(s));
+    CK(prepare_buffers(ctx, ctx->b));
+    CK(enqueue_match(ctx, rows_dev, row_cap, row_stride, true));
+    CKC(cudaStreamSynchronize(ctx->stream));
     GmStatus &st = *ctx->h_st;
     if (st.err == 0 && st.nitems > (uint64_t)ctx->items_cap) {
       int64_t need = (int64_t)(st.nitems + (st.nitems >> 2) + 1024);
       ctx->items_cap = 0;
       CK(ensure(ctx->d_items, ctx->items_cap, need));
-      continue;  // redo with room for every item
+      continue;
     }
-    ctx->stats.ms_seed = ev_ms(ctx->ev[2], ctx->ev[3]);
-    ctx->stats.ms_match = ev_ms(ctx->ev[3], ctx->ev[4]);
-    ctx->stats.ms_finalize = ev_ms(ctx->ev[4], ctx->ev[5]);
-    ctx->stats.seeds = (int64_t)st.nseeds;
-    ctx->stats.work_items = (int64_t)st.nitems;
-    ctx->stats.expansions = st.expansions;
-    ctx->stats.alg_bytes = st.alg_bytes;
+    match_stats(ctx);
     return GAMMA_OK;
   }
   return ctx->fail(GAMMA_ENOMEM, "work item buffer kept overflowing");
+}
+
+// rows destination for a gamma_matches request (device pointer to write)
+int rows_target(gamma_ctx *ctx, gamma_matches *out, int32_t **rows, bool *dev) {
+  *rows = nullptr;
+  *dev = false;
+  if (!out) return GAMMA_OK;
+  if (out->capacity < 0 || (out->capacity > 0 && !out->rows)) return ctx->fail(GAMMA_EINVAL, "bad gamma_matches buffer");
+  int need_stride = 3 + 2;
+  for (int32_t id : ctx->qids) need_stride = std::max(need_stride, 3 + ctx->queries[id].q);
+  if (out->stride < need_stride) return ctx->fail(GAMMA_EINVAL, "gamma_matches.stride %d < %d", out->stride, need_stride);
+  *dev = is_device_ptr(out->rows);
+  *rows = out->rows;
+  if (!*dev) {
+    CK(ensure(ctx->d_rows, ctx->rows_cap, std::max<int64_t>(out->capacity * out->stride, 1)));
+    *rows = ctx->d_rows;
+  }
+  return GAMMA_OK;
 }
 
 int copy_rows_out(gamma_ctx *ctx, gamma_matches *out, bool dev_rows) {
@@ -429,21 +525,158 @@ int copy_rows_out(gamma_ctx *ctx, gamma_matches *out, bool dev_rows) {
 }
 
 int match_with_rows(gamma_ctx *ctx, gamma_matches *out) {
-  if (!out) return run_match(ctx, nullptr, 0, 0);
-  if (out->capacity < 0 || (out->capacity > 0 && !out->rows)) return ctx->fail(GAMMA_EINVAL, "bad gamma_matches buffer");
-  int need_stride = 3 + 2;
-  for (int32_t id : ctx->qids) need_stride = std::max(need_stride, 3 + ctx->queries[id].q);
-  if (out->stride < need_stride) return ctx->fail(GAMMA_EINVAL, "gamma_matches.stride %d < %d", out->stride, need_stride);
-  bool dev = is_device_ptr(out->rows);
-  int32_t *rows = out->rows;
-  if (!dev) {
-    CK(ensure(ctx->d_rows, ctx->rows_cap, std::max<int64_t>(out->capacity * out->stride, 1)));
-    rows = ctx->d_rows;
-  }
-  int rc = run_match(ctx, rows, (uint64_t)out->capacity, out->stride);
+  int32_t *rows;
+  bool dev;
+  CK(rows_target(ctx, out, &rows, &dev));
+  int rc = run_match(ctx, rows, out ? (uint64_t)out->capacity : 0, out ? out->stride : 0);
   if (rc) return rc;
-  if (ctx->h_st->err) return GAMMA_OK;  // reported by the caller
+  if (!out || ctx->h_st->err) return GAMMA_OK;  // errors are reported by the caller
   return copy_rows_out(ctx, out, dev);
+}
+
+// stage + match in one stream sequence (optionally replayed as a CUDA graph),
+// one host sync; retried after growing the adjacency pool or the item buffer
+int run_apply(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const int32_t *ddst, int32_t *rows,
+              uint64_t row_cap, int row_stride) {
+  cudaStream_t s = ctx->stream;
+  for (int attempt = 0; attempt < 4; attempt++) {
+    CK(prepare_buffers(ctx, ctx->b));
+    reset_status_host(ctx);
+    if (ctx->flags & GAMMA_F_GRAPH) {
+      std::vector<int64_t> key = {ctx->b, ctx->nreq, (int64_t)ctx->flags, ctx->tile, ctx->wpb, ctx->grain,
+                                  (int64_t)ctx->budget, (int64_t)(intptr_t)rows, (int64_t)row_cap, row_stride,
+                                  (int64_t)(intptr_t)dop, (int64_t)(intptr_t)dsrc, (int64_t)(intptr_t)ddst,
+                                  (int64_t)(intptr_t)ctx->d_col, (int64_t)(intptr_t)ctx->d_etag, ctx->pool_cap,
+                                  (int64_t)(intptr_t)ctx->d_items, ctx->items_cap, (int64_t)(intptr_t)ctx->d_plans,
+                                  (int64_t)(intptr_t)ctx->d_pair_off, (int64_t)(intptr_t)ctx->d_pair_plans,
+                                  (int64_t)(intptr_t)ctx->sb.cu, (int64_t)(intptr_t)ctx->d_cnt,
+                                  (int64_t)(intptr_t)ctx->d_per_upd, (int64_t)(intptr_t)ctx->d_req,
+                                  (int64_t)(intptr_t)ctx->h_cnt, ctx->nplans, ctx->maxq};
+      key.insert(key.end(), ctx->plan_key.begin(), ctx->plan_key.end());
+      if (key != ctx->gkey || !ctx->gexec) {
+        cudaGraph_t graph = nullptr;
+        CKC(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        int rc1 = enqueue_stage(ctx, dop, dsrc, ddst);
+        int rc2 = rc1 ? rc1 : enqueue_match(ctx, rows, row_cap, row_stride, false);
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (rc2) { if (graph) cudaGraphDestroy(graph); return ctx->cuda_fail(rc2); }
+        CKC(ce);
+        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        cudaError_t ie = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        CKC(ie);
+        ctx->gkey = key;
+        ctx->graph_captures++;
+      }
+      CKC(cudaGraphLaunch(ctx->gexec, s));
+    } else {
+      CK(enqueue_stage(ctx, dop, dsrc, ddst));
+      CK(enqueue_match(ctx, rows, row_cap, row_stride, false));
+    }
+    CKC(cudaStreamSynchronize(s));
+    GmStatus &st = *ctx->h_st;
+    if (st.err == GAMMA_ENOMEM) {  // the stage changed nothing; grow the pool and redo
+      CK(grow_pool(ctx, ctx->pool_top + st.reloc_total));
+      continue;
+    }
+    // a stage error (invalid batch) leaves the graph unchanged; a timeout is
+    // raised by the match phase, after the batch was staged
+    if (st.err && st.err != GAMMA_ETIMEOUT) return GAMMA_OK;  // reported by the caller
+    ctx->pool_top = st.pool_top;
+    ctx->hub_top = st.hub_top;
+    ctx->stats.ms_stage = ev_ms(ctx->ev[0], ctx->ev[1]);
+    ctx->stats.touched = st.ntouched;
+    ctx->staged = true;
+    if (!st.err && st.nitems > (uint64_t)ctx->items_cap) {  // staged; redo the match phase with more room
+      int64_t need = (int64_t)(st.nitems + (st.nitems >> 2) + 1024);
+      ctx->items_cap = 0;
+      CK(ensure(ctx->d_items, ctx->items_cap, need));
+      return run_match(ctx, rows, row_cap, row_stride);
+    }
+    match_stats(ctx);
+    return GAMMA_OK;
+  }
+  return ctx->fail(GAMMA_ENOMEM, "apply kept running out of device memory");
+}
+
+int apply_impl(gamma_ctx *ctx, const char *fn, int32_t nreq, const int64_t *req_off, int64_t b, const int8_t *op,
+               const int32_t *src, const int32_t *dst, int32_t nq, const int32_t *qids, uint64_t *out_pos,
+               uint64_t *out_neg, gamma_matches *opt_out) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "%s: no graph loaded", fn);
+  if (ctx->staged) return ctx->fail(GAMMA_ESTATE, "%s: previous batch not committed", fn);
+  if (b < 0 || b >= ((int64_t)1 << 31) || nq < 0 || nreq < 1 || (b > 0 && (!op || !src || !dst)) ||
+      (nq > 0 && (!qids || !out_pos || !out_neg)))
+    return ctx->fail(GAMMA_EINVAL, "%s: bad sizes or null arrays", fn);
+  for (int j = 0; j < nq; j++)
+    if (qids[j] < 0 || qids[j] >= (int)ctx->queries.size())
+      return ctx->fail(GAMMA_EINVAL, "%s: unknown query id %d", fn, qids[j]);
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  ctx->b = b;
+  ctx->nreq = nreq;
+  ctx->qids.assign(qids, qids + nq);
+  int rc = prepare_buffers(ctx, b);
+  if (rc) return ctx->err.empty() ? ctx->cuda_fail(rc) : rc;
+  if (nreq > 1) {
+    std::vector<uint32_t> req(b);
+    for (int r = 0; r < nreq; r++) {
+      if (req_off[r] > req_off[r + 1] || req_off[r] < 0 || req_off[r + 1] > b)
+        return ctx->fail(GAMMA_EINVAL, "%s: bad request offsets", fn);
+      for (int64_t k = req_off[r]; k < req_off[r + 1]; k++) req[k] = (uint32_t)r;
+    }
+    if (req_off[0] != 0 || req_off[nreq] != b) return ctx->fail(GAMMA_EINVAL, "%s: request offsets must cover the batch", fn);
+    CKC(cudaMemcpyAsync(ctx->d_req, req.data(), sizeof(uint32_t) * b, cudaMemcpyHostToDevice, s));
+    CKC(cudaStreamSynchronize(s));
+  }
+  const int8_t *dop = op;
+  const int32_t *dsrc = src, *ddst = dst;
+  if (b > 0) {
+    bool dev = is_device_ptr(op) && is_device_ptr(src) && is_device_ptr(dst);
+    if (!dev || (ctx->flags & GAMMA_F_GRAPH)) {  // the graph reads fixed staging buffers
+      CKC(cudaMemcpyAsync(ctx->d_in_op, op, b, cudaMemcpyDefault, s));
+      CKC(cudaMemcpyAsync(ctx->d_in_src, src, 4 * b, cudaMemcpyDefault, s));
+      CKC(cudaMemcpyAsync(ctx->d_in_dst, dst, 4 * b, cudaMemcpyDefault, s));
+      dop = ctx->d_in_op; dsrc = ctx->d_in_src; ddst = ctx->d_in_dst;
+    }
+  }
+  int32_t *rows;
+  bool devrows;
+  rc = rows_target(ctx, opt_out, &rows, &devrows);
+  if (rc) return rc;
+  rc = run_apply(ctx, dop, dsrc, ddst, rows, opt_out ? (uint64_t)opt_out->capacity : 0, opt_out ? opt_out->stride : 0);
+  if (rc) return ctx->err.empty() ? ctx->fail(rc, "%s failed", fn) : rc;
+  GmStatus st = *ctx->h_st;
+  if (!ctx->staged) {
+    if (st.err == GAMMA_EINVAL) {
+      if (st.bad_index != INT64_MAX)
+        return ctx->fail(GAMMA_EINVAL,
+                         "%s: update %lld is invalid (bad op or id, self-loop, repeated edge, "
+                         "insertion of an existing edge or deletion of a missing one); graph unchanged",
+                         fn, (long long)st.bad_index);
+      return ctx->fail(GAMMA_EINVAL, "%s: invalid batch; graph unchanged", fn);
+    }
+    return ctx->fail(st.err ? st.err : GAMMA_ECUDA, "%s: staging failed (code %d)", fn, st.err);
+  }
+  for (int r = 0; r < nreq; r++)
+    for (int j = 0; j < nq; j++) {
+      out_pos[(int64_t)r * nq + j] = ctx->h_cnt[((int64_t)r * nq + j) * 2];
+      out_neg[(int64_t)r * nq + j] = ctx->h_cnt[((int64_t)r * nq + j) * 2 + 1];
+    }
+  ctx->stats.pool_used = (int64_t)ctx->pool_top;
+  ctx->stats.pool_cap = ctx->pool_cap;
+  if (st.err == GAMMA_ETIMEOUT)
+    return ctx->fail(GAMMA_ETIMEOUT, "%s: work budget exceeded or a wait timed out; counts are incomplete", fn);
+  if (st.err) return ctx->fail(st.err, "%s: matching failed (code %d)", fn, st.err);
+  if (opt_out) {
+    rc = copy_rows_out(ctx, opt_out, devrows);
+    if (rc == GAMMA_EOVERFLOW)
+      return ctx->fail(GAMMA_EOVERFLOW, "%s: %lld match rows do not fit in %lld", fn, (long long)opt_out->required,
+                       (long long)opt_out->capacity);
+    if (rc) return rc;
+  }
+  return GAMMA_OK;
 }
 
 }  // namespace
@@ -481,7 +714,8 @@ int gamma_create(const gamma_options *options, gamma_ctx **out) {
     ctx->own_stream = true;
   }
   if (cudaMalloc((void **)&ctx->d_st, sizeof(GmStatus)) != cudaSuccess ||
-      cudaMallocHost((void **)&ctx->h_st, sizeof(GmStatus)) != cudaSuccess) {
+      cudaMallocHost((void **)&ctx->h_st, sizeof(GmStatus)) != cudaSuccess ||
+      cudaMallocHost((void **)&ctx->h_st_init, sizeof(GmStatus)) != cudaSuccess) {
     gamma_destroy(ctx);
     return GAMMA_ENOMEM;
   }
@@ -499,9 +733,11 @@ void gamma_destroy(gamma_ctx *ctx) {
   void *ps[] = {sb.cu, sb.cv, sb.cop, sb.keys, sb.tk, sb.vals, sb.tv, sb.head, sb.gid, sb.gv, sb.gstart,
                 sb.gins, sb.greloc, sb.bkeys, ctx->d_in_op, ctx->d_in_src, ctx->d_in_dst, ctx->d_plans,
                 ctx->d_pair_off, ctx->d_pair_plans, ctx->d_items, ctx->d_cnt, ctx->d_per_upd, ctx->d_rows,
-                ctx->d_tasks, ctx->d_task_seq, ctx->d_sched, ctx->d_st};
+                ctx->d_tasks, ctx->d_task_seq, ctx->d_sched, ctx->d_req, ctx->d_st};
   for (void *p : ps) if (p) cudaFree(p);
   if (ctx->h_st) cudaFreeHost(ctx->h_st);
+  if (ctx->h_st_init) cudaFreeHost(ctx->h_st_init);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
   for (auto &e : ctx->ev) if (e) cudaEventDestroy(e);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -509,6 +745,12 @@ void gamma_destroy(gamma_ctx *ctx) {
 }
 
 const char *gamma_last_error(gamma_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+}  // extern "C"
+
+int gm_ctx_device(gamma_ctx *ctx) { return ctx->device; }
+
+extern "C" {
 
 int gamma_set_options(gamma_ctx *ctx, const gamma_options *o) {
   if (!ctx || !o) return GAMMA_EINVAL;
@@ -553,7 +795,7 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
     dd = td;
   }
   reset_status_host(ctx);
-  CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
+  CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st_init, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
   CK(gm_load_validate(dl, n, ds, dd, m, ctx->d_st, s));
   CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
   CKC(cudaStreamSynchronize(s));
@@ -583,6 +825,8 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
   CKC(cudaMalloc((void **)&ctx->d_adj, sizeof(uint2) * n));
   CKC(cudaMalloc((void **)&ctx->d_cap, sizeof(uint32_t) * n));
   CKC(cudaMalloc((void **)&ctx->d_nlf, (size_t)n * ctx->nlfw));
+  CKC(cudaMalloc((void **)&ctx->d_vgroup, sizeof(int32_t) * n));
+  CKC(cudaMemsetAsync(ctx->d_vgroup, 0xff, sizeof(int32_t) * n, s));
   CKC(cudaMemsetAsync(ctx->d_nlf, 0, (size_t)n * ctx->nlfw, s));
   uint32_t pool_cap = 0;
   GraphDev g = ctx->gd();
@@ -638,7 +882,7 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
       }
       ctx->hub_top = 0;
       reset_status_host(ctx);
-      CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
+      CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st_init, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
       CK(gm_hub(ctx->gd(), nullptr, nullptr, (uint32_t)n, ctx->d_st, s));
       CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
       CKC(cudaStreamSynchronize(s));
@@ -700,101 +944,17 @@ int gamma_register_query(gamma_ctx *ctx, int32_t q, const int32_t *qlabels, int3
 int gamma_apply_batch(gamma_ctx *ctx, int64_t b, const int8_t *op, const int32_t *src, const int32_t *dst,
                       int32_t nq, const int32_t *qids, uint64_t *out_pos, uint64_t *out_neg,
                       gamma_matches *opt_out) {
+  const int64_t off[2] = {0, b};
+  return apply_impl(ctx, "gamma_apply_batch", 1, off, b, op, src, dst, nq, qids, out_pos, out_neg, opt_out);
+}
+
+int gamma_apply_batches(gamma_ctx *ctx, int32_t nreq, const int64_t *req_off, const int8_t *op,
+                        const int32_t *src, const int32_t *dst, int32_t nq, const int32_t *qids,
+                        uint64_t *out_pos, uint64_t *out_neg) {
   if (!ctx) return GAMMA_EINVAL;
-  ctx->err.clear();
-  if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "gamma_apply_batch: no graph loaded");
-  if (ctx->staged) return ctx->fail(GAMMA_ESTATE, "gamma_apply_batch: previous batch not committed");
-  if (b < 0 || b >= ((int64_t)1 << 31) || nq < 0 || (b > 0 && (!op || !src || !dst)) ||
-      (nq > 0 && (!qids || !out_pos || !out_neg)))
-    return ctx->fail(GAMMA_EINVAL, "gamma_apply_batch: bad sizes or null arrays");
-  for (int j = 0; j < nq; j++)
-    if (qids[j] < 0 || qids[j] >= (int)ctx->queries.size())
-      return ctx->fail(GAMMA_EINVAL, "gamma_apply_batch: unknown query id %d", qids[j]);
-  cudaSetDevice(ctx->device);
-  cudaStream_t s = ctx->stream;
-  StageBufs &sb = ctx->sb;
-  if (b > sb.cap) {
-    int64_t c = std::max<int64_t>(b, 1024);
-    void *ps[] = {sb.cu, sb.cv, sb.cop, sb.keys, sb.tk, sb.vals, sb.tv, sb.head, sb.gid, sb.gv, sb.gstart,
-                  sb.gins, sb.greloc, sb.bkeys};
-    for (void *p : ps) if (p) cudaFree(p);
-    sb = StageBufs();
-    CKC(cudaMalloc((void **)&sb.cu, 4 * c)); CKC(cudaMalloc((void **)&sb.cv, 4 * c));
-    CKC(cudaMalloc((void **)&sb.cop, c));
-    CKC(cudaMalloc((void **)&sb.keys, 16 * c)); CKC(cudaMalloc((void **)&sb.tk, 16 * c));
-    CKC(cudaMalloc((void **)&sb.vals, 8 * c)); CKC(cudaMalloc((void **)&sb.tv, 8 * c));
-    CKC(cudaMalloc((void **)&sb.head, 8 * c)); CKC(cudaMalloc((void **)&sb.gid, 8 * c));
-    CKC(cudaMalloc((void **)&sb.gv, 8 * c)); CKC(cudaMalloc((void **)&sb.gstart, 8 * c));
-    CKC(cudaMalloc((void **)&sb.gins, 8 * c)); CKC(cudaMalloc((void **)&sb.greloc, 8 * c));
-    CKC(cudaMalloc((void **)&sb.bkeys, 8 * c));
-    sb.cap = c;
-  }
-  const int8_t *dop = op;
-  const int32_t *dsrc = src, *ddst = dst;
-  if (b > 0) {
-    bool dev = is_device_ptr(op) && is_device_ptr(src) && is_device_ptr(dst);
-    if (!dev) {
-      if (b > ctx->in_cap) {
-        cudaFree(ctx->d_in_op); cudaFree(ctx->d_in_src); cudaFree(ctx->d_in_dst);
-        ctx->d_in_op = nullptr; ctx->d_in_src = nullptr; ctx->d_in_dst = nullptr;
-        int64_t c = std::max<int64_t>(b, 1024);
-        CKC(cudaMalloc((void **)&ctx->d_in_op, c));
-        CKC(cudaMalloc((void **)&ctx->d_in_src, 4 * c));
-        CKC(cudaMalloc((void **)&ctx->d_in_dst, 4 * c));
-        ctx->in_cap = c;
-      }
-      CKC(cudaMemcpyAsync(ctx->d_in_op, op, b, cudaMemcpyDefault, s));
-      CKC(cudaMemcpyAsync(ctx->d_in_src, src, 4 * b, cudaMemcpyDefault, s));
-      CKC(cudaMemcpyAsync(ctx->d_in_dst, dst, 4 * b, cudaMemcpyDefault, s));
-      dop = ctx->d_in_op; dsrc = ctx->d_in_src; ddst = ctx->d_in_dst;
-    }
-  }
-  for (int attempt = 0; attempt < 3; attempt++) {
-    reset_status_host(ctx);
-    CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
-    CKC(cudaEventRecord(ctx->ev[0], s));
-    if (b > 0) CK(gm_stage(ctx->gd(), dop, dsrc, ddst, b, sb, ctx->d_st, s));
-    CKC(cudaEventRecord(ctx->ev[1], s));
-    CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
-    CKC(cudaStreamSynchronize(s));
-    if (ctx->h_st->err == GAMMA_ENOMEM) {
-      CK(grow_pool(ctx, ctx->pool_top + ctx->h_st->reloc_total));
-      continue;
-    }
-    break;
-  }
-  GmStatus st0 = *ctx->h_st;
-  if (st0.err == GAMMA_EINVAL) {
-    if (st0.bad_index != INT64_MAX)
-      return ctx->fail(GAMMA_EINVAL,
-                       "gamma_apply_batch: update %lld is invalid (bad op or id, self-loop, repeated edge, "
-                       "insertion of an existing edge or deletion of a missing one); graph unchanged",
-                       (long long)st0.bad_index);
-    return ctx->fail(GAMMA_EINVAL, "gamma_apply_batch: invalid batch; graph unchanged");
-  }
-  if (st0.err) return ctx->fail(st0.err, "gamma_apply_batch: staging failed (code %d)", st0.err);
-  ctx->stats.ms_stage = ev_ms(ctx->ev[0], ctx->ev[1]);
-  ctx->pool_top = st0.pool_top;
-  ctx->hub_top = st0.hub_top;
-  ctx->stats.touched = st0.ntouched;
-  ctx->b = b;
-  ctx->staged = true;
-  ctx->qids.assign(qids, qids + nq);
-  int rc = match_with_rows(ctx, opt_out);
-  if (rc != GAMMA_OK && rc != GAMMA_EOVERFLOW) return ctx->err.empty() ? ctx->fail(rc, "match failed") : rc;
-  for (int j = 0; j < nq; j++) {
-    out_pos[j] = ctx->h_cnt[2 * j];
-    out_neg[j] = ctx->h_cnt[2 * j + 1];
-  }
-  ctx->stats.pool_used = (int64_t)ctx->pool_top;
-  ctx->stats.pool_cap = ctx->pool_cap;
-  if (ctx->h_st->err == GAMMA_ETIMEOUT)
-    return ctx->fail(GAMMA_ETIMEOUT, "gamma_apply_batch: work budget exceeded; counts are incomplete");
-  if (ctx->h_st->err) return ctx->fail(ctx->h_st->err, "gamma_apply_batch: matching failed (code %d)", ctx->h_st->err);
-  if (rc == GAMMA_EOVERFLOW)
-    return ctx->fail(GAMMA_EOVERFLOW, "gamma_apply_batch: %lld match rows do not fit in %lld",
-                     (long long)opt_out->required, (long long)opt_out->capacity);
-  return GAMMA_OK;
+  if (nreq < 1 || !req_off) return ctx->fail(GAMMA_EINVAL, "gamma_apply_batches: need nreq >= 1 and offsets");
+  return apply_impl(ctx, "gamma_apply_batches", nreq, req_off, req_off[nreq], op, src, dst, nq, qids, out_pos,
+                    out_neg, nullptr);
 }
 
 int gamma_fetch_matches(gamma_ctx *ctx, gamma_matches *out) {
@@ -880,6 +1040,7 @@ int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out) {
   out->pool_cap = ctx->pool_cap;
   out->live_edges = ctx->live;
   out->kernel_launches = __atomic_load_n(&gm_launch_count, __ATOMIC_RELAXED);
+  out->graph_captures = ctx->graph_captures;
   return GAMMA_OK;
 }
 

@@ -58,6 +58,7 @@ struct GraphDev {
   uint32_t *col;         // [pool] adjacency keys
   uint32_t *etag;        // [pool] batch tag of flagged entries
   uint8_t *nlf;          // [n * nlfw] per-label neighbour counts of the union graph, saturated at 255
+  int32_t *vgroup;       // [n] while a batch is staged: the vertex's group in the sorted batch, else -1
   // hub index: vertices whose list had >= GM_HUB_MIN entries at load keep the
   // start of every label segment and an open-addressing hash set of their keys
   const int32_t *hub_id; // [n] hub number or -1

@@ -365,7 +365,10 @@ __global__ void k_stage_merge(GraphDev g, const uint64_t *__restrict__ keys, con
       }
     }
     __syncwarp();
-    if (lane == 0) g.adj[v] = make_uint2(off, tot);
+    if (lane == 0) {
+      g.adj[v] = make_uint2(off, tot);
+      g.vgroup[v] = (int32_t)gi;
+    }
   }
 }
 
@@ -396,6 +399,7 @@ __global__ void k_commit(GraphDev g, const uint32_t *__restrict__ gv, const uint
     }
     if (lane == 0) {
       g.adj[v] = make_uint2(a.x, out);
+      g.vgroup[v] = -1;
       // change of this list's committed length: insertions - deletions
       int64_t delta = (int64_t)gins[gi] - (int64_t)(a.y - out);
       if (delta) atomicAdd((unsigned long long *)&st->live, (unsigned long long)delta);

@@ -42,7 +42,9 @@ struct MatchArgs {
   int grain;                   // level-2 candidates per work item
   WorkItem *items;
   uint64_t item_cap;
-  uint64_t *cnt;               // [nq * 2] positive / negative counts
+  uint64_t *cnt;               // [nreq * nq * 2] positive / negative counts
+  const uint32_t *req;         // [b] request of each update (null: one request)
+  int nq;                      // query slots per request
   uint64_t *per_upd;           // [nq * b] or null
   int use_filter;
   int32_t *rows;               // match rows or null
@@ -53,6 +55,12 @@ struct MatchArgs {
   int nlev;                    // stored DFS levels (max q - 3, >= 1)
   int warps_per_block;
   int count_bytes;             // accumulate algorithmic bytes into st->alg_bytes
+  int leaf;                    // count a last position with one backward neighbour in closed form
+  const uint64_t *bkeys;       // the staged batch, sorted: (vertex << 33 | deletion << 32 | key)
+  const uint32_t *bvals;       // its tags
+  const uint32_t *gstart;      // [groups] first sorted entry of each touched vertex
+  const uint32_t *gins;        // [groups] insertions of each touched vertex (they come first)
+  uint32_t n2;                 // sorted entries (2 per update)
   Task *tasks;                 // donated work (null: no donation)
   uint32_t *sched;             // [GM_SCHED_WORDS] scheduling counters
   uint32_t *task_seq;          // [task_cap] 1 once the task in the slot is written

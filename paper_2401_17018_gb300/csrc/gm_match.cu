@@ -34,8 +34,21 @@ __device__ __forceinline__ int warp_read(const int32_t *p) {
   return __shfl_sync(GM_FULL, v, 0);
 }
 
-__device__ __forceinline__ bool tag_ok(uint32_t t, uint32_t sdel, uint32_t upd) {
-  return ((t & 1u) == sdel) && ((t >> 1) > upd);
+// Visibility of a batch-tagged edge (tag = update index << 1 | deletion) to a
+// seed of update `upd` with sign `sdel` from request `r`.  Same request: the
+// seed's view (G' for insertions, G for deletions) plus the charging rule
+// (only same-sign updates of larger index).  Several requests staged together
+// are applied in order: an earlier request's insertion is already present and
+// its deletion already gone; a later request's insertion is not there yet and
+// its deletion has not happened yet.
+__device__ __forceinline__ bool tag_ok(uint32_t t, uint32_t sdel, uint32_t upd, const uint32_t *req,
+                                       uint32_t r) {
+  const uint32_t k = t >> 1, d = t & 1u;
+  if (req) {
+    const uint32_t rk = __ldg(req + k);
+    if (rk != r) return (rk < r) ? (d == 0u) : (d == 1u);
+  }
+  return d == sdel && k > upd;
 }
 
 // is the edge (w, c) visible in the seed's view under the charging rule?
@@ -48,7 +61,7 @@ __device__ __forceinline__ uint32_t probe_bytes(uint32_t d) {
 }
 
 __device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t x, uint32_t sdel,
-                                        uint32_t upd, uint64_t &bytes) {
+                                        uint32_t upd, const uint32_t *req, uint32_t r, uint64_t &bytes) {
   const uint32_t key = x & ~1u;
   const int32_t h = __ldg(g.hub_id + w);
   if (h >= 0) {
@@ -78,7 +91,7 @@ __device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t 
   if (p >= a.y) return false;
   uint32_t y = __ldg(L + p);
   if ((y | 1u) != (key | 1u)) return false;
-  if (y & 1u) return tag_ok(__ldg(g.etag + a.x + p), sdel, upd);
+  if (y & 1u) return tag_ok(__ldg(g.etag + a.x + p), sdel, upd, req, r);
   return true;
 }
 
@@ -182,7 +195,8 @@ __global__ void k_seed(MatchArgs a) {
         if (P.q == 2) {
           if (pass == 0) {
             my_seeds++;
-            atomicAdd((unsigned long long *)&a.cnt[P.qslot * 2 + sdel], 1ull);
+            const uint32_t rq = a.req ? a.req[k] : 0u;
+            atomicAdd((unsigned long long *)&a.cnt[((uint64_t)rq * a.nq + P.qslot) * 2 + sdel], 1ull);
             if (a.per_upd) atomicAdd((unsigned long long *)&a.per_upd[(uint64_t)P.qslot * a.b + k], 1ull);
             if (a.rows) {
               uint64_t r = atomicAdd((unsigned long long *)&st->rows, 1ull);
@@ -340,6 +354,7 @@ __global__ void k_dfs(MatchArgs a) {
 
   if (warp_read(&st->err)) return;
   const uint64_t nitems = min(*(volatile uint64_t *)&st->nitems, a.item_cap);
+  const uint32_t ntouched = *(volatile uint32_t *)&st->ntouched;
   int cur_plan = -1;
   bool items_done = false;
 
@@ -431,6 +446,7 @@ __global__ void k_dfs(MatchArgs a) {
     const int q = P.q, last = q - 1;
     const uint32_t m0 = __ldg(a.cu + upd), m1 = __ldg(a.cv + upd);
     const uint32_t sdel = a.op[upd] < 0 ? 1u : 0u;
+    const uint32_t rq = a.req ? __ldg(a.req + upd) : 0u;
     uint64_t wcount = 0;
     uint64_t lbytes = 0;  // this lane's algorithmic bytes (only reported with count_bytes)
     uint32_t chunks = 0;
@@ -567,6 +583,105 @@ __global__ void k_dfs(MatchArgs a) {
         continue;
       }
       const bool stored = (c != last);
+      if (!stored && a.leaf && !a.rows && __popc((uint32_t)P.bwd[c]) == 1) {
+        // The last vertex hangs on a single earlier vertex (a degree-1 query
+        // vertex, Sec. V-B Remark): every slot of its driver slice is a match
+        // except batch-tagged entries this seed must not see and vertices the
+        // partial match already uses, so count the slice instead of visiting it.
+        const int lab = P.lab[c];
+        const uint16_t same = P.samelab[c];
+        uint64_t add = 0;
+        uint32_t nent = 1;
+        // drop from len the slots of [lo, lo + len) in N^lab(v) the seed cannot use
+        auto slice_count = [&](uint32_t v, uint32_t lo, uint32_t len, uint32_t k_lo, uint32_t k_hi) -> uint64_t {
+          uint64_t cntv = len;
+          const int32_t gi = __ldg(g.vgroup + v);
+          lbytes += 12;
+          if (gi >= 0) {  // v's batch entries: insertions, then deletions, each sorted by key
+            const uint32_t s0 = __ldg(a.gstart + gi), ni = __ldg(a.gins + gi);
+            const uint32_t e1 = ((uint32_t)gi + 1 < ntouched) ? __ldg(a.gstart + gi + 1) : a.n2;
+            for (int part = 0; part < 2; part++) {
+              const uint32_t pb = part ? s0 + ni : s0, pe = part ? e1 : s0 + ni;
+              uint32_t l2 = pb, h2 = pe;
+              while (l2 < h2) {
+                const uint32_t mid = (l2 + h2) >> 1;
+                if (((uint32_t)__ldg(a.bkeys + mid) & ~1u) < k_lo) l2 = mid + 1; else h2 = mid;
+              }
+              lbytes += 32u * (32u - __clz((pe - pb) | 1u));
+              for (uint32_t j = l2; j < pe; j++) {
+                const uint32_t kj = (uint32_t)__ldg(a.bkeys + j) & ~1u;
+                lbytes += 12;
+                if (kj > k_hi) break;
+                if (!tag_ok(__ldg(a.bvals + j), sdel, upd, a.req, rq)) cntv--;
+              }
+            }
+          }
+          return cntv;
+        };
+        // a same-label vertex of the partial match inside the slice is not a new match
+        auto conflict = [&](uint32_t v, uint32_t mv, uint32_t k_lo, uint32_t k_hi) -> uint32_t {
+          const uint32_t kj = gm_key(lab, mv, g.idb);
+          if (kj < k_lo || kj > k_hi) return 0u;
+          return edge_ok(g, v, kj, sdel, upd, a.req, rq, lbytes) ? 1u : 0u;
+        };
+        if (lev < 0) {
+          if (lane == 0) {
+            const uint32_t v = root_drv ? m1 : m0, lo = root_lo + cur, len = total - cur;
+            const uint32_t k_lo = __ldg(g.col + lo) & ~1u, k_hi = __ldg(g.col + lo + len - 1) & ~1u;
+            uint64_t cv = slice_count(v, lo, len, k_lo, k_hi);
+            if (root_drv != 0 && (same & 1u)) cv -= conflict(v, m0, k_lo, k_hi);
+            if (root_drv != 1 && (same & 2u)) cv -= conflict(v, m1, k_lo, k_hi);
+            add = cv;
+          }
+        } else {
+          const uint32_t n = H->cnt[lev];
+          const uint32_t *ex = EX + lev * T;
+          auto entry_of = [&](uint32_t x) {  // last entry with ex <= x
+            uint32_t lo = 0, hi = n;
+            while (hi - lo > 1) {
+              uint32_t mid = (lo + hi) >> 1;
+              if (ex[mid] <= x) lo = mid; else hi = mid;
+            }
+            return lo;
+          };
+          const uint32_t e0 = entry_of(cur), e1 = entry_of(total - 1);
+          nent = e1 - e0 + 1;
+          for (uint32_t e = e0 + lane; e <= e1; e += 32) {
+            const uint32_t elen = ((e + 1 < n) ? ex[e + 1] : H->full[lev]) - ex[e];
+            const uint32_t a0 = max(cur, ex[e]), a1 = min(total, ex[e] + elen);
+            if (a1 <= a0) continue;
+            const uint32_t lo = LO[lev * T + e] + (a0 - ex[e]), len = a1 - a0;
+            const int dp = DRV[lev * T + e];
+            // the driver's vertex, from the chain of entry e
+            uint32_t v = (dp == 0) ? m0 : m1;
+            {
+              uint32_t ee = e;
+              for (int l2 = lev; l2 >= 0; l2--) {
+                if (l2 + 2 == dp) v = V[l2 * T + ee];
+                ee = PAR[l2 * T + ee];
+              }
+            }
+            const uint32_t k_lo = __ldg(g.col + lo) & ~1u, k_hi = __ldg(g.col + lo + len - 1) & ~1u;
+            uint64_t cv = slice_count(v, lo, len, k_lo, k_hi);
+            uint32_t ee = e;
+            for (int l2 = lev; l2 >= 0; l2--) {
+              const int pos = l2 + 2;
+              if (pos != dp && ((same >> pos) & 1u)) cv -= conflict(v, V[l2 * T + ee], k_lo, k_hi);
+              ee = PAR[l2 * T + ee];
+            }
+            if (dp != 1 && ((same >> 1) & 1u)) cv -= conflict(v, m1, k_lo, k_hi);
+            if (dp != 0 && (same & 1u)) cv -= conflict(v, m0, k_lo, k_hi);
+            add += cv;
+          }
+        }
+        for (int d = 16; d > 0; d >>= 1) add += __shfl_xor_sync(GM_FULL, add, d);
+        wcount += add;
+        chunks += (nent + 31) / 32;
+        if (lev < 0) root_cur = total;
+        else if (lane == 0) H->cur[lev] = total;
+        __syncwarp();
+        continue;
+      }
       if (stored && H->cnt[lev + 1] + 32 > (uint32_t)T) {
         prepare(lev + 1);
         lev++;
@@ -595,7 +710,7 @@ __global__ void k_dfs(MatchArgs a) {
       chunks++;
       uint32_t x = ok ? __ldg(g.col + slot2) : 0u;
       const uint32_t id = (x >> 1) & g.idmask;
-      if (ok && (x & 1u)) ok = tag_ok(__ldg(g.etag + slot2), sdel, upd);
+      if (ok && (x & 1u)) ok = tag_ok(__ldg(g.etag + slot2), sdel, upd, a.req, rq);
       const uint16_t chk_edge = P.bwd[c] & (uint16_t)~(1u << drv);
       const uint16_t chk_neq = P.samelab[c];
       if (ok && (chk_edge | chk_neq)) {
@@ -604,13 +719,13 @@ __global__ void k_dfs(MatchArgs a) {
           const int pos = l2 + 2;
           const uint32_t vv = V[l2 * T + ee];
           if ((chk_neq >> pos) & 1) ok = (vv != id);
-          if (ok && ((chk_edge >> pos) & 1)) ok = edge_ok(g, vv, x, sdel, upd, lbytes);
+          if (ok && ((chk_edge >> pos) & 1)) ok = edge_ok(g, vv, x, sdel, upd, a.req, rq, lbytes);
           ee = PAR[l2 * T + ee];
         }
         if (ok && ((chk_neq >> 1) & 1)) ok = (m1 != id);
-        if (ok && ((chk_edge >> 1) & 1)) ok = edge_ok(g, m1, x, sdel, upd, lbytes);
+        if (ok && ((chk_edge >> 1) & 1)) ok = edge_ok(g, m1, x, sdel, upd, a.req, rq, lbytes);
         if (ok && (chk_neq & 1)) ok = (m0 != id);
-        if (ok && (chk_edge & 1)) ok = edge_ok(g, m0, x, sdel, upd, lbytes);
+        if (ok && (chk_edge & 1)) ok = edge_ok(g, m0, x, sdel, upd, a.req, rq, lbytes);
       }
       if (ok && stored && a.use_filter) ok = nlf_ok(g, id, P, c);
       if (gidx < total) lbytes += ((x & 1u) ? 8u : 4u) + (ok ? 8u : 0u);
@@ -669,7 +784,7 @@ __global__ void k_dfs(MatchArgs a) {
     }
     if (lane == 0) {
       if (wcount) {
-        atomicAdd((unsigned long long *)&a.cnt[P.qslot * 2 + sdel], (unsigned long long)wcount);
+        atomicAdd((unsigned long long *)&a.cnt[((uint64_t)rq * a.nq + P.qslot) * 2 + sdel], (unsigned long long)wcount);
         if (a.per_upd)
           atomicAdd((unsigned long long *)&a.per_upd[(uint64_t)P.qslot * a.b + upd], (unsigned long long)wcount);
       }

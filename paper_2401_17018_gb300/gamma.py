@@ -19,8 +19,8 @@ from . import build as _build
 
 GAMMA_OK, GAMMA_EINVAL, GAMMA_ENOMEM, GAMMA_ESTATE, GAMMA_EOVERFLOW, GAMMA_ETIMEOUT, GAMMA_ECUDA = (
     0, -1, -2, -3, -4, -5, -6)
-GAMMA_F_PER_UPDATE, GAMMA_F_NO_FILTER, GAMMA_F_PER_QUERY, GAMMA_F_GRAPH, GAMMA_F_COUNT_BYTES = (
-    0x1, 0x2, 0x4, 0x8, 0x10)
+GAMMA_F_PER_UPDATE, GAMMA_F_NO_FILTER, GAMMA_F_PER_QUERY, GAMMA_F_GRAPH, GAMMA_F_COUNT_BYTES, GAMMA_F_NO_LEAF = (
+    0x1, 0x2, 0x4, 0x8, 0x10, 0x20)
 
 _NAMES = {0: "GAMMA_OK", -1: "GAMMA_EINVAL", -2: "GAMMA_ENOMEM", -3: "GAMMA_ESTATE",
           -4: "GAMMA_EOVERFLOW", -5: "GAMMA_ETIMEOUT", -6: "GAMMA_ECUDA"}
@@ -42,7 +42,22 @@ class gamma_stats(ctypes.Structure):
                 ("ms_finalize", ctypes.c_double), ("ms_commit", ctypes.c_double), ("seeds", ctypes.c_int64),
                 ("work_items", ctypes.c_int64), ("touched", ctypes.c_int64), ("pool_used", ctypes.c_int64),
                 ("pool_cap", ctypes.c_int64), ("live_edges", ctypes.c_int64), ("expansions", ctypes.c_uint64),
-                ("alg_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+                ("alg_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("graph_captures", ctypes.c_int64)]
+
+
+class gamma_server_options(ctypes.Structure):
+    _fields_ = [("max_updates", ctypes.c_int64), ("max_requests", ctypes.c_int32), ("hbm_fraction", ctypes.c_double)]
+
+
+class gamma_request_info(ctypes.Structure):
+    _fields_ = [("arrival_ms", ctypes.c_double), ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
+                ("group_size", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class gamma_server_stats(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int64), ("requests", ctypes.c_int64), ("updates", ctypes.c_int64),
+                ("max_group", ctypes.c_int64), ("busy_ms", ctypes.c_double)]
 
 
 class GammaError(RuntimeError):
@@ -60,6 +75,7 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int32)]),
     "gamma_apply_batch": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int32, _P, _P, _P,
                                          ctypes.POINTER(gamma_matches)]),
+    "gamma_apply_batches": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, _P, _P]),
     "gamma_fetch_matches": (ctypes.c_int, [_P, ctypes.POINTER(gamma_matches)]),
     "gamma_update_counts": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "gamma_commit": (ctypes.c_int, [_P]),
@@ -67,6 +83,12 @@ _SIGS = {
     "gamma_export_adjacency": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
     "gamma_set_options": (ctypes.c_int, [_P, ctypes.POINTER(gamma_options)]),
     "gamma_last_error": (ctypes.c_char_p, [_P]),
+    "gamma_server_start": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(gamma_server_options),
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "gamma_server_submit": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    "gamma_server_wait": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.POINTER(gamma_request_info)]),
+    "gamma_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(gamma_server_stats)]),
+    "gamma_server_stop": (ctypes.c_int, [_P]),
 }
 
 _lib = None
@@ -164,6 +186,19 @@ def gamma_apply_batch(ctx: int, op, src, dst, qids: Sequence[int], matches: Opti
     if rc not in (GAMMA_OK, GAMMA_EOVERFLOW):
         _check(ctx, rc)
     return pos[:q.size], neg[:q.size], rc
+
+
+def gamma_apply_batches(ctx: int, req_off, op, src, dst, qids: Sequence[int]) -> Tuple[np.ndarray, np.ndarray]:
+    """Several requests staged together; returns (pos, neg) of shape [nreq, nq]."""
+    off = np.ascontiguousarray(req_off, dtype=np.int64)
+    nreq = off.size - 1
+    op, src, dst = _as(op, np.int8), _as(src, np.int32), _as(dst, np.int32)
+    q = np.ascontiguousarray(qids, dtype=np.int32)
+    pos = np.zeros(max(nreq * q.size, 1), np.uint64)
+    neg = np.zeros(max(nreq * q.size, 1), np.uint64)
+    _check(ctx, load_library().gamma_apply_batches(ctx, nreq, _ptr(off), _ptr(op), _ptr(src), _ptr(dst), int(q.size),
+                                                   _ptr(q), _ptr(pos), _ptr(neg)))
+    return pos[:nreq * q.size].reshape(nreq, q.size), neg[:nreq * q.size].reshape(nreq, q.size)
 
 
 def gamma_fetch_matches(ctx: int, matches: gamma_matches) -> int:
@@ -279,6 +314,10 @@ class Context:
             return pos, neg
         return pos, neg, buf[:m.written], m.required
 
+    def apply_batches(self, req_off, op, src, dst, qids: Sequence[int]):
+        self.b = int(op.shape[0])
+        return gamma_apply_batches(self.h, req_off, op, src, dst, qids)
+
     def fetch_matches(self, rows):
         m = gamma_matches(_ptr(rows), int(rows.shape[0]), int(rows.shape[1]), 0, 0)
         gamma_fetch_matches(self.h, m)
@@ -296,3 +335,65 @@ class Context:
     def export_adjacency(self, n: int):
         st = self.stats()
         return gamma_export_adjacency(self.h, n, int(st["pool_used"]))
+
+
+# ----------------------------------------------------------- served form
+def gamma_server_start(ctx: int, qids: Sequence[int], options: Optional[gamma_server_options] = None) -> int:
+    q = np.ascontiguousarray(qids, dtype=np.int32)
+    out = ctypes.c_void_p()
+    rc = load_library().gamma_server_start(ctx, int(q.size), _ptr(q), ctypes.byref(options) if options else None,
+                                           ctypes.byref(out))
+    if rc != GAMMA_OK:
+        raise GammaError(rc, "gamma_server_start failed")
+    return out.value
+
+
+def gamma_server_submit(srv: int, op, src, dst) -> int:
+    op, src, dst = _as(op, np.int8), _as(src, np.int32), _as(dst, np.int32)
+    t = ctypes.c_int64(-1)
+    rc = load_library().gamma_server_submit(srv, int(op.shape[0]), _ptr(op), _ptr(src), _ptr(dst), ctypes.byref(t))
+    if rc != GAMMA_OK:
+        raise GammaError(rc, "gamma_server_submit failed")
+    return t.value
+
+
+def gamma_server_wait(srv: int, ticket: int, nq: int):
+    """(status, pos[nq], neg[nq], info dict) of one finished request."""
+    pos = np.zeros(max(nq, 1), np.uint64)
+    neg = np.zeros(max(nq, 1), np.uint64)
+    info = gamma_request_info()
+    rc = load_library().gamma_server_wait(srv, int(ticket), _ptr(pos), _ptr(neg), ctypes.byref(info))
+    return rc, pos[:nq], neg[:nq], {k: getattr(info, k) for k, _ in gamma_request_info._fields_}
+
+
+def gamma_server_stats_get(srv: int) -> dict:
+    st = gamma_server_stats()
+    load_library().gamma_server_stats_get(srv, ctypes.byref(st))
+    return {k: getattr(st, k) for k, _ in gamma_server_stats._fields_}
+
+
+def gamma_server_stop(srv: int) -> None:
+    load_library().gamma_server_stop(srv)
+
+
+class Server:
+    """Served form on a Context: submit requests, wait for their counts."""
+
+    def __init__(self, ctx: Context, qids: Sequence[int], max_updates: int = 0, max_requests: int = 0,
+                 hbm_fraction: float = 0.0):
+        self.nq = len(qids)
+        self.h = gamma_server_start(ctx.h, qids, gamma_server_options(max_updates, max_requests, hbm_fraction))
+
+    def submit(self, op, src, dst) -> int:
+        return gamma_server_submit(self.h, op, src, dst)
+
+    def wait(self, ticket: int):
+        return gamma_server_wait(self.h, ticket, self.nq)
+
+    def stats(self) -> dict:
+        return gamma_server_stats_get(self.h)
+
+    def stop(self):
+        if self.h:
+            gamma_server_stop(self.h)
+            self.h = None

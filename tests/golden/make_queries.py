@@ -34,8 +34,11 @@ SPECS = {
     "batched": ("mid", 90_000, 10_000,
                 [("sparse" if i % 2 == 0 else "dense", 4 + (i * 7) % 9) for i in range(64)]),
 }
-STRIDE = 200
-BUDGET = 10_000_000
+# (stride, budget) per query class: every stride-th update of the batch is
+# evaluated, within budget candidate tests. Sparse queries on the power-law
+# graphs are far costlier per update, so they get a thinner sample and a
+# larger budget.
+RULES = {"dense": (200, 10_000_000), "sparse": (2500, 40_000_000), "tree": (2500, 40_000_000)}
 
 _W = None
 
@@ -56,10 +59,11 @@ def _try(args):
     Q = I.random_walk_query(off, nbr, g.labels, q, kind, w.seed + 1000 * q, attempt)
     if Q is None:
         return attempt, None, "class test failed"
-    ev = np.arange(0, len(b), STRIDE)
+    stride, budget = RULES[kind]
+    ev = np.arange(0, len(b), stride)
     t = time.time()
     try:
-        c, _ = O.bdsm(g.n, g.labels, g.src, g.dst, Q, b, eval_idx=ev, budget=BUDGET)
+        c, _ = O.bdsm(g.n, g.labels, g.src, g.dst, Q, b, eval_idx=ev, budget=budget)
     except O.OracleError as e:
         return attempt, Q.to_json(), "oracle budget exceeded on the sample (code %d)" % e.code
     if int(c.sum()) == 0:
@@ -79,20 +83,39 @@ def main():
     _init(args.name)
     w = _W[0]
     out = {"workload": wl, "graph_digest": w.graph.digest(), "batch": {"n_ins": ni, "n_del": nd, "sub": 0},
-           "rule": "keep a candidate when the CPU oracle finishes it on updates 0, %d, 2*%d, ... of the batch "
-                   "within %d candidate tests and finds at least one incremental match there" % (
-                       STRIDE, STRIDE, BUDGET),
+           "rule": "keep a candidate of class k when the CPU oracle finishes it on updates 0, s, 2s, ... of the "
+                   "batch within B candidate tests and finds at least one incremental match there; (s, B) per "
+                   "class: " + json.dumps(RULES),
            "queries": [], "rejected": []}
     want = {}
     for kind, q in plan:
         want[(kind, q)] = want.get((kind, q), 0) + 1
     chosen = {k: [] for k in want}
     seen = set()
+    path = os.path.join(HERE, "queries_%s.json" % args.name)
+    partial = path + ".partial"
+    start_at = {}
+    if os.path.exists(partial):  # resume: keep what an interrupted run chose
+        with open(partial) as f:
+            old = json.load(f)
+        for d in old["chosen"]:
+            key = (d["kind"], len(d["labels"]))
+            if key in chosen and len(chosen[key]) < want[key]:
+                chosen[key].append(d)
+                seen.add(json.dumps([d["labels"], d["edges"]]))
+        out["rejected"] = old["rejected"]
+        start_at = {tuple(k.split(":")): v for k, v in old.get("next_attempt", {}).items()}
+
+    def save_partial(next_attempt):
+        with open(partial, "w") as f:
+            json.dump({"chosen": [d for v in chosen.values() for d in v], "rejected": out["rejected"],
+                       "next_attempt": {"%s:%d" % k: v for k, v in next_attempt.items()}}, f)
     ctx = get_context("fork")
     with ctx.Pool(args.workers) as pool:
+        next_attempt = {}
         for (kind, q), need in sorted(want.items()):
-            attempt = 0
-            while len(chosen[(kind, q)]) < need and attempt < 4000:
+            attempt = int(start_at.get((kind, str(q)), 0))
+            while len(chosen[(kind, q)]) < need and attempt < 20000:
                 jobs = [(kind, q, attempt + i) for i in range(args.workers * 2)]
                 attempt += len(jobs)
                 for att, d, why in pool.map(_try, jobs):
@@ -104,10 +127,13 @@ def main():
                             continue
                         seen.add(key)
                         d["attempt"] = att
+                        d["kind"] = kind
                         chosen[(kind, q)].append(d)
                         print("keep", kind, q, att, d["sample_matches"], flush=True)
                     elif d is not None:
                         out["rejected"].append({"kind": kind, "q": q, "attempt": att, "why": why})
+                next_attempt[(kind, q)] = attempt
+                save_partial(next_attempt)
             if len(chosen[(kind, q)]) < need:
                 raise SystemExit("could not find %d %s queries of %d vertices" % (need, kind, q))
     # emit in the order of the plan
@@ -115,9 +141,10 @@ def main():
     for kind, q in plan:
         out["queries"].append(chosen[(kind, q)][used[(kind, q)]])
         used[(kind, q)] += 1
-    path = os.path.join(HERE, "queries_%s.json" % args.name)
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
+    if os.path.exists(partial):
+        os.remove(partial)
     print("wrote", path, len(out["queries"]), "queries,", len(out["rejected"]), "rejected")
 
 

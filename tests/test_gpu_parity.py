@@ -118,10 +118,12 @@ def test_tiny_workload_mixed_many_queries(G):
         if q is not None:
             qs.append(q)
     check(G, g, qs, b)
+    check(G, g, qs, b, rows=False)
 
 
+@pytest.mark.parametrize("rows", [True, False])
 @pytest.mark.parametrize("trial", range(40))
-def test_fuzz_small_graphs(G, trial):
+def test_fuzz_small_graphs(G, trial, rows):
     r = np.random.default_rng(1000 + trial)
     n = int(r.integers(6, 40))
     g = I.random_small_graph(n, int(r.integers(10, 60)), int(r.integers(1, 4)), 9, trial)
@@ -150,7 +152,8 @@ def test_fuzz_small_graphs(G, trial):
                 edges.append((a, c))
         qs.append(I.pattern_query(r.integers(0, nl, q).tolist(), edges))
     flags = [0, 2, 4][trial % 3]
-    check(G, g, qs, b, flags=flags, frontier_tile=[32, 64, 128][trial % 3], steal_grain=[1, 3, 64][trial % 3])
+    check(G, g, qs, b, rows=rows, flags=flags, frontier_tile=[32, 64, 128][trial % 3],
+          steal_grain=[1, 3, 64][trial % 3])
 
 
 def test_empty_batch_and_no_queries(G):
@@ -250,7 +253,8 @@ def test_options_do_not_change_results(G):
     b = I.workload_batch(w, 500, 200, sub=3)
     qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 0, 1, 1], [(0, 1), (1, 2), (2, 3), (3, 0)])]
     ref = None
-    for flags, tile, grain, wpb in [(0, 64, 64, 8), (2, 32, 1, 4), (4, 128, 7, 16), (6, 256, 1024, 2)]:
+    for flags, tile, grain, wpb in [(0, 64, 64, 8), (2, 32, 1, 4), (4, 128, 7, 16), (6, 256, 1024, 2), (32, 64, 64, 8),
+                                    (8, 64, 64, 8)]:
         pos, neg, _, _, _ = gpu_run(G, w.graph, qs, b, flags=flags, rows=False, frontier_tile=tile,
                                     steal_grain=grain, warps_per_block=wpb)
         got = (pos.tolist(), neg.tolist())
@@ -307,3 +311,130 @@ def test_work_budget_times_out_cleanly(G):
         b2 = I.workload_batch(w, 10, 0, pool_start=300)
         ctx.apply_batch(b2.op, b2.src, b2.dst, [qid])
         ctx.commit()
+
+
+def test_graph_mode_replays_and_matches(G):
+    """GAMMA_F_GRAPH: the apply is captured once per shape and replayed; counts unchanged."""
+    w = I.make_workload("tiny")
+    b = I.workload_batch(w, 300, 100, sub=4)
+    inv = b.inverse()
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)])]
+    ref = []
+    for flags in [0, G.GAMMA_F_GRAPH]:
+        got = []
+        with G.Context(flags=flags) as ctx:
+            ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+            qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+            for k in range(4):
+                bb = b if k % 2 == 0 else inv
+                pos, neg = ctx.apply_batch(bb.op, bb.src, bb.dst, qids)
+                got.append((pos.tolist(), neg.tolist()))
+                ctx.commit()
+            st = ctx.stats()
+        if flags:
+            assert st["graph_captures"] == 1
+            assert got == ref
+        else:
+            ref = got
+    for j, q in enumerate(qs):
+        c, _ = O.bdsm(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst, q, b)
+        assert (ref[0][0][j], ref[0][1][j]) == O.totals(c, b.op)
+
+
+def _requests(w, sizes, seed):
+    """Consecutive requests on disjoint edges: insertions from the pool, deletions from G0."""
+    g = w.graph
+    reqs = []
+    start, dstart = 0, 0
+    order = np.random.default_rng(seed).permutation(g.src.size)
+    for i, n in enumerate(sizes):
+        ni = n * 3 // 4
+        nd = n - ni
+        s = np.concatenate([w.pool_src[start:start + ni], g.src[order[dstart:dstart + nd]]])
+        d = np.concatenate([w.pool_dst[start:start + ni], g.dst[order[dstart:dstart + nd]]])
+        op = np.concatenate([np.ones(ni, np.int8), -np.ones(nd, np.int8)])
+        p = np.random.default_rng(seed + i).permutation(n)
+        reqs.append(I.Batch(op[p], s[p].astype(np.int32), d[p].astype(np.int32)))
+        start += ni
+        dstart += nd
+    return reqs
+
+
+@pytest.mark.parametrize("flags", [0, 4, 8])
+def test_requests_alone_equal_in_the_mix(G, flags):
+    """Several requests staged together give each request the result it gets alone."""
+    w = I.make_workload("tiny")
+    reqs = _requests(w, [40, 1, 130, 75, 9, 200], 5)
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)]), I.pattern_query([1, 1], [(0, 1)])]
+    alone = []
+    with G.Context() as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        for r in reqs:
+            pos, neg = ctx.apply_batch(r.op, r.src, r.dst, qids)
+            alone.append((pos.tolist(), neg.tolist()))
+            ctx.commit()
+        after_alone = ctx.export_adjacency(w.graph.n)
+    with G.Context(flags=flags) as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        off = np.concatenate([[0], np.cumsum([len(r) for r in reqs])])
+        cat = lambda f: np.concatenate([getattr(r, f) for r in reqs])
+        pos, neg = ctx.apply_batches(off, cat("op"), cat("src"), cat("dst"), qids)
+        ctx.commit()
+        after_mix = ctx.export_adjacency(w.graph.n)
+    assert [(pos[r].tolist(), neg[r].tolist()) for r in range(len(reqs))] == alone
+    assert np.array_equal(after_alone[0], after_mix[0])
+    # oracle, request by request
+    cs, cd = w.graph.src, w.graph.dst
+    for r, rb in enumerate(reqs):
+        for j, q in enumerate(qs):
+            c, _ = O.bdsm(w.graph.n, w.graph.labels, cs, cd, q, rb)
+            assert (int(pos[r, j]), int(neg[r, j])) == O.totals(c, rb.op)
+        cs, cd = I.apply_batch_edges(cs, cd, rb)
+
+
+def test_requests_touching_the_same_edge_are_rejected(G):
+    w = I.make_workload("tiny")
+    e = (int(w.pool_src[0]), int(w.pool_dst[0]))
+    op = np.array([1, -1], np.int8)
+    src = np.array([e[0], e[0]], np.int32)
+    dst = np.array([e[1], e[1]], np.int32)
+    with G.Context() as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qid = ctx.register_query([0, 1], [0], [1])
+        with pytest.raises(G.GammaError) as ex:
+            ctx.apply_batches(np.array([0, 1, 2]), op, src, dst, [qid])
+        assert ex.value.code == G.GAMMA_EINVAL
+
+
+def test_server_results_equal_sequential(G):
+    """Served form: every request's counts equal those of applying the requests
+    one by one, and requests that queued while the GPU was busy were staged together."""
+    w = I.make_workload("tiny")
+    reqs = _requests(w, [int(x) for x in np.random.default_rng(9).integers(1, 30, 40)], 11)
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)])]
+    alone = []
+    with G.Context() as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        for r in reqs:
+            pos, neg = ctx.apply_batch(r.op, r.src, r.dst, qids)
+            alone.append((pos.tolist(), neg.tolist()))
+            ctx.commit()
+    with G.Context() as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        srv = G.Server(ctx, qids, max_requests=16)
+        tickets = [srv.submit(r.op, r.src, r.dst) for r in reqs]
+        got, groups = [], []
+        for t in tickets:
+            rc, pos, neg, info = srv.wait(t)
+            assert rc == G.GAMMA_OK
+            got.append((pos.tolist(), neg.tolist()))
+            groups.append(info["group_size"])
+            assert info["done_ms"] >= info["start_ms"] >= info["arrival_ms"] - 1e-6
+        st = srv.stats()
+        srv.stop()
+    assert got == alone
+    assert max(groups) > 1 and st["requests"] == len(reqs) and st["groups"] < len(reqs)
