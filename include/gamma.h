@@ -185,6 +185,21 @@ GAMMA_API int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out);
  * 0 keeps the current value for the three tuning fields). */
 GAMMA_API int gamma_set_options(gamma_ctx *ctx, const gamma_options *options);
 
+/* Recount the staged batch without allocating anything: re-runs the DFS
+ * kernel over the batch's work items (kept by the last gamma_apply_batch or
+ * gamma_apply_batches) and writes the counts to host arrays out_pos / out_neg
+ * (nreq * nq entries, laid out as for gamma_apply_batches).  No counterpart in
+ * the paper.  It is for callers that must not allocate at that moment, e.g.
+ * while recording a CUDA graph in global capture mode or when another
+ * allocator owns the device memory: the DFS scratch (task queue, scheduling
+ * counters, counts) lives in a static device array of about 1.2 MB that every
+ * GPU loading the library holds until exit.  Limits: nreq * nq <= 256
+ * (GAMMA_EINVAL beyond), the batched form only (not GAMMA_F_PER_QUERY).  The
+ * first call on a device looks up the array's address; make it before any
+ * stream capture.  All calls share the array and each clears what must start
+ * at zero; calls that overlap on the GPU race and must not be issued. */
+GAMMA_API int gamma_recount_noalloc(gamma_ctx *ctx, uint64_t *out_pos, uint64_t *out_neg);
+
 /* ------------------------------------------------------------------------
  * Served form: a worker thread applies a stream of update requests to the
  * device-resident graph, in arrival order.  Requests that arrive while the

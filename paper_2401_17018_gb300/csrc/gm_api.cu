@@ -750,6 +750,50 @@ const char *gamma_last_error(gamma_ctx *ctx) { return ctx ? ctx->err.c_str() : "
 
 int gm_ctx_device(gamma_ctx *ctx) { return ctx->device; }
 
+// Arguments for re-running the DFS over the work items of the staged batch,
+// from buffers the context already holds (nothing is allocated here).  The
+// caller supplies the counts, task queue and scheduling scratch.
+int gm_recount_prepare(gamma_ctx *ctx, MatchArgs *a, int *nslots, int *num_sms, cudaStream_t *stream) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->staged) return ctx->fail(GAMMA_ESTATE, "no staged batch to recount");
+  if (ctx->flags & GAMMA_F_PER_QUERY)
+    return ctx->fail(GAMMA_ESTATE, "the recount needs the batched form (GAMMA_F_PER_QUERY keeps one query's items)");
+  if (ctx->h_st->err) return ctx->fail(GAMMA_ESTATE, "the staged batch's matching failed (code %d)", ctx->h_st->err);
+  if (ctx->h_st->nitems > (uint64_t)ctx->items_cap) return ctx->fail(GAMMA_ESTATE, "work items of the batch were not kept");
+  const int nq = (int)ctx->qids.size();
+  *nslots = std::max(nq, 1) * ctx->nreq;
+  *num_sms = ctx->num_sms;
+  *stream = ctx->stream;
+  MatchArgs &m = *a;
+  m.g = ctx->gd();
+  m.cu = ctx->sb.cu; m.cv = ctx->sb.cv; m.op = ctx->sb.cop; m.b = ctx->b;
+  m.plans = ctx->d_plans; m.nplans = ctx->nplans;
+  m.pair_off = ctx->d_pair_off; m.pair_plans = ctx->d_pair_plans;
+  m.grain = ctx->grain;
+  m.items = ctx->d_items; m.item_cap = (uint64_t)ctx->items_cap;
+  m.cnt = nullptr;
+  m.req = (ctx->nreq > 1) ? ctx->d_req : nullptr;
+  m.nq = std::max(nq, 1);
+  m.per_upd = nullptr;
+  m.use_filter = (ctx->flags & GAMMA_F_NO_FILTER) ? 0 : 1;
+  m.rows = nullptr; m.row_cap = 0; m.row_stride = 0;
+  m.budget = ctx->budget;
+  m.tile = ctx->tile;
+  m.nlev = std::max(1, ctx->maxq - 3);
+  m.warps_per_block = ctx->wpb;
+  m.count_bytes = 0;
+  m.leaf = (ctx->flags & GAMMA_F_NO_LEAF) ? 0 : 1;
+  m.bkeys = ctx->sb.keys; m.bvals = ctx->sb.vals; m.gstart = ctx->sb.gstart; m.gins = ctx->sb.gins;
+  m.n2 = (uint32_t)(2 * ctx->b);
+  m.tasks = nullptr; m.sched = nullptr; m.task_seq = nullptr; m.task_cap = 0;
+  m.idle_limit_ns = 60ull * 1000000000ull;
+  m.st = ctx->d_st;
+  return GAMMA_OK;
+}
+
+int gm_ctx_fail(gamma_ctx *ctx, int code, const char *msg) { return ctx->fail(code, "%s", msg); }
+
 extern "C" {
 
 int gamma_set_options(gamma_ctx *ctx, const gamma_options *o) {

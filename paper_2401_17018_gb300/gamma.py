@@ -83,6 +83,7 @@ _SIGS = {
     "gamma_export_adjacency": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
     "gamma_set_options": (ctypes.c_int, [_P, ctypes.POINTER(gamma_options)]),
     "gamma_last_error": (ctypes.c_char_p, [_P]),
+    "gamma_recount_noalloc": (ctypes.c_int, [_P, _P, _P]),
     "gamma_server_start": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(gamma_server_options),
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "gamma_server_submit": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.POINTER(ctypes.c_int64)]),
@@ -335,6 +336,14 @@ class Context:
     def export_adjacency(self, n: int):
         st = self.stats()
         return gamma_export_adjacency(self.h, n, int(st["pool_used"]))
+
+
+def gamma_recount_noalloc(ctx: int, nslots: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Counts of the staged batch recomputed without allocating (see gamma.h)."""
+    pos = np.zeros(max(nslots, 1), np.uint64)
+    neg = np.zeros(max(nslots, 1), np.uint64)
+    _check(ctx, load_library().gamma_recount_noalloc(ctx, _ptr(pos), _ptr(neg)))
+    return pos[:nslots], neg[:nslots]
 
 
 # ----------------------------------------------------------- served form
