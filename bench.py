@@ -40,6 +40,10 @@ import numpy as np  # noqa: E402
 
 WORKLOADS = {
     "mid": {"workload": "mid", "queries": "tests/golden/queries_mid.json", "n_ins": 90_000, "n_del": 10_000},
+    # the same graph, queries and batch cut to its first 3,000 updates: a case
+    # small enough for multi-pass profiler captures
+    "mid_3k": {"workload": "mid", "queries": "tests/golden/queries_mid.json", "n_ins": 90_000, "n_del": 10_000,
+               "first": 3000},
     "tiny": {"workload": "tiny", "queries": None, "n_ins": 256, "n_del": 0},
 }
 METRIC = "updates/s & incremental matches/s per batch (1 GB300); p50/p99 batch latency"
@@ -59,6 +63,9 @@ def load_workload(name):
     else:
         queries = [I.TRIANGLE_WITH_TAIL]
     batch = I.workload_batch(w, spec["n_ins"], spec["n_del"])
+    if "first" in spec:
+        k = spec["first"]
+        batch = I.Batch(batch.op[:k].copy(), batch.src[:k].copy(), batch.dst[:k].copy())
     return w, queries, batch
 
 
@@ -198,6 +205,7 @@ def config_of(workload, b, nq):
     spec = WORKLOADS[workload]
     return {"workload": "%s: R-MAT %s, %d queries, batch %d (%d ins + %d del)" % (
         workload, {"mid": "scale 20, 7.55M edges, 8 labels Zipf(1.2)",
+                   "mid_3k": "scale 20, 7.55M edges, 8 labels Zipf(1.2), first 3,000 updates of the mid batch",
                    "tiny": "scale 11, 9k edges, 4 labels"}[workload], nq, b, spec["n_ins"], spec["n_del"]),
         "batch_updates": b, "queries": nq, "l2": "flushed before every timed step (256 MiB write)",
         "step": "apply batch (stage+seed+DFS+counts to host) + commit; batch and inverse alternate"}
@@ -206,7 +214,7 @@ def config_of(workload, b, nq):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gamma", choices=["gamma", "reference"])
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))

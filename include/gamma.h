@@ -67,7 +67,7 @@ typedef struct {
   void *cuda_stream;     /* cudaStream_t to run on; NULL = a stream owned by the context */
   uint32_t flags;        /* GAMMA_F_* */
   uint64_t work_budget;  /* max 32-candidate expansion steps per apply; 0 = unlimited */
-  int warps_per_block;   /* DFS kernel warps per block; 0 = 8 */
+  int warps_per_block;   /* DFS kernel warps per block (1..16); 0 = 8 */
   int frontier_tile;     /* partial matches buffered per DFS level per warp (32..256); 0 = 64 */
   int steal_grain;       /* level-2 candidates per work item; 0 = 64 */
 } gamma_options;

@@ -705,7 +705,7 @@ int gamma_create(const gamma_options *options, gamma_ctx **out) {
   if (o.warps_per_block > 0) ctx->wpb = o.warps_per_block;
   if (o.frontier_tile > 0) ctx->tile = o.frontier_tile;
   if (o.steal_grain > 0) ctx->grain = o.steal_grain;
-  if (ctx->tile < 32 || ctx->tile > 4096 || ctx->wpb > 32) { delete ctx; return GAMMA_EINVAL; }
+  if (ctx->tile < 32 || ctx->tile > 4096 || ctx->wpb > 16) { delete ctx; return GAMMA_EINVAL; }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, o.device);
   if (o.cuda_stream) {
     ctx->stream = (cudaStream_t)o.cuda_stream;
@@ -800,7 +800,7 @@ int gamma_set_options(gamma_ctx *ctx, const gamma_options *o) {
   if (!ctx || !o) return GAMMA_EINVAL;
   if (o->frontier_tile && (o->frontier_tile < 32 || o->frontier_tile > 4096))
     return ctx->fail(GAMMA_EINVAL, "frontier_tile must be in [32, 4096]");
-  if (o->warps_per_block < 0 || o->warps_per_block > 32) return ctx->fail(GAMMA_EINVAL, "warps_per_block must be in [1, 32]");
+  if (o->warps_per_block < 0 || o->warps_per_block > 16) return ctx->fail(GAMMA_EINVAL, "warps_per_block must be in [1, 16]");
   ctx->flags = o->flags;
   ctx->budget = o->work_budget;
   if (o->warps_per_block) ctx->wpb = o->warps_per_block;
