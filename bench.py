@@ -47,7 +47,7 @@ WORKLOADS = {
     "tiny": {"workload": "tiny", "queries": None, "n_ins": 256, "n_del": 0},
 }
 METRIC = "updates/s & incremental matches/s per batch (1 GB300); p50/p99 batch latency"
-STATUS_BYTES = 104  # the library's status block, read back after staging, matching and commit
+STATUS_BYTES = 112  # the library's status block, read back after staging, matching and commit
 
 
 def load_workload(name):

@@ -99,6 +99,7 @@ typedef struct {
   uint64_t alg_bytes;  /* DFS algorithmic bytes of the last apply (GAMMA_F_COUNT_BYTES) */
   uint64_t kernel_launches; /* kernels the library has launched in this process so far */
   int64_t graph_captures;   /* CUDA graphs captured by this context (GAMMA_F_GRAPH) */
+  int64_t donated_tasks;    /* work pieces idle warps received from busy ones in the last DFS launch */
 } gamma_stats;
 
 /* Create a context on options->device (options may be NULL: defaults).

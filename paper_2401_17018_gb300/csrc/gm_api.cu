@@ -475,6 +475,7 @@ void match_stats(gamma_ctx *ctx) {
   ctx->stats.work_items = (int64_t)st.nitems;
   ctx->stats.expansions = st.expansions;
   ctx->stats.alg_bytes = st.alg_bytes;
+  ctx->stats.donated_tasks = st.tasks_donated;
 }
 
 // the match phase alone, with retries when the work item buffer was too small

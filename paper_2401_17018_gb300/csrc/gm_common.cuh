@@ -40,6 +40,8 @@ struct GmStatus {
   uint64_t garbage;       // slots freed by relocation
   uint32_t max_label;     // load: largest vertex label
   uint32_t hub_top;       // hub hash slots allocated
+  uint32_t tasks_donated; // tasks the last DFS launch split off
+  uint32_t pad;
 };
 
 // DFS scheduling counters, one per 128-byte line (reset before every DFS launch)

@@ -312,18 +312,33 @@ __device__ bool idle_wait(const MatchArgs &a, uint64_t &slot) {
   }
 }
 
-// lane 0 of a busy warp: reserve n consecutive task slots (never past the
-// capacity) and count their future runners as busy
+// lane 0 of a busy warp: reserve n consecutive task numbers and count their
+// future runners as busy.  Task number r lives in ring slot r mod capacity.
 __device__ bool reserve_tasks(const MatchArgs &a, uint32_t n, uint32_t &base) {
   uint32_t *sched = a.sched;
+  if (n > a.task_cap) return false;
   atomicAdd(sched + GM_SCHED_BUSY, n);
-  for (int tries = 0; tries < 64; tries++) {
-    uint32_t r = vload(sched + GM_SCHED_RESERVE);
-    if ((uint64_t)r + n > a.task_cap) break;
-    if (atomicCAS(sched + GM_SCHED_RESERVE, r, r + n) == r) { base = r; return true; }
+  base = atomicAdd(sched + GM_SCHED_RESERVE, n);
+  return true;
+}
+
+// write task number r into its ring slot: wait (bounded) until the slot's
+// previous task has been read, then publish r + 1 in the slot's word
+__device__ bool publish_task(const MatchArgs &a, uint32_t r, const Task &t) {
+  const uint32_t ph = r & (a.task_cap - 1u);
+  const uint64_t t0 = global_ns();
+  while (vload(&a.task_seq[ph]) != 0u) {
+    if (global_ns() - t0 > 1000000000ull) {
+      gm_set_err(a.st, GAMMA_ETIMEOUT);
+      atomicExch(&a.st->abort, 1);
+      return false;
+    }
+    __nanosleep(64);
   }
-  atomicSub(sched + GM_SCHED_BUSY, n);
-  return false;
+  a.tasks[ph] = t;
+  __threadfence();
+  *(volatile uint32_t *)&a.task_seq[ph] = r + 1u;
+  return true;
 }
 
 // tickets waiting for a slot (warp-uniform)
@@ -374,7 +389,7 @@ __global__ void k_dfs(MatchArgs a) {
       }
       if (kind == 2) {  // the donor publishes right after reserving; wait for it (bounded)
         const uint64_t t0 = global_ns();
-        while (vload(&a.task_seq[slot]) != 1u) {
+        while (vload(&a.task_seq[slot & (a.task_cap - 1u)]) != (uint32_t)slot + 1u) {
           if (global_ns() - t0 > 1000000000ull) {
             gm_set_err(st, GAMMA_ETIMEOUT);
             atomicExch(&st->abort, 1);
@@ -399,8 +414,12 @@ __global__ void k_dfs(MatchArgs a) {
       // WorkItem {upd, plan|drv<<16|pad<<24, lo, len} -> task words {upd, plan|depth|drv, lo, len}
       if (lane == 1) word = (word & 0xffffu) | (0xffu << 16) | (((word >> 16) & 0xffu) << 24);
     } else {
-      const uint32_t *src = reinterpret_cast<const uint32_t *>(a.tasks + slot);
+      const uint32_t ph = (uint32_t)slot & (a.task_cap - 1u);
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(a.tasks + ph);
       if (lane < 16) word = __ldcg(src + lane);
+      __syncwarp();
+      __threadfence();
+      if (lane == 0) *(volatile uint32_t *)&a.task_seq[ph] = 0u;  // the ring slot is free again
     }
     const uint32_t upd = __shfl_sync(GM_FULL, word, 0);
     const uint32_t w1 = __shfl_sync(GM_FULL, word, 1);
@@ -516,11 +535,10 @@ __global__ void k_dfs(MatchArgs a) {
         uint32_t base = 0;
         int ok = 0;
         if (lane == 0 && reserve_tasks(a, 1, base)) {
-          Task *t = a.tasks + base;
-          t->upd = upd; t->plan = (uint16_t)plan; t->depth = -1; t->drv = (uint8_t)root_drv;
-          t->lo = root_lo + s; t->len = t0 - s;
-          __threadfence();
-          *(volatile uint32_t *)&a.task_seq[base] = 1u;
+          Task t;
+          t.upd = upd; t.plan = (uint16_t)plan; t.depth = -1; t.drv = (uint8_t)root_drv;
+          t.lo = root_lo + s; t.len = t0 - s;
+          publish_task(a, base, t);
           ok = 1;
         }
         if (__shfl_sync(GM_FULL, ok, 0)) root_len = s;
@@ -552,17 +570,16 @@ __global__ void k_dfs(MatchArgs a) {
         const uint32_t e = e_first + lane;
         const uint32_t elen = ((e + 1 < n) ? ex[e + 1] : H->full[L]) - ex[e];
         const uint32_t a0 = max(s2, ex[e]), a1 = min(t0, ex[e] + elen);
-        Task *t = a.tasks + base + lane;
-        t->upd = upd; t->plan = (uint16_t)plan; t->depth = (int8_t)L; t->drv = DRV[L * T + e];
-        t->lo = LO[L * T + e] + (a0 - ex[e]);
-        t->len = a1 - a0;
+        Task t;
+        t.upd = upd; t.plan = (uint16_t)plan; t.depth = (int8_t)L; t.drv = DRV[L * T + e];
+        t.lo = LO[L * T + e] + (a0 - ex[e]);
+        t.len = a1 - a0;
         uint32_t ee = e;
         for (int l2 = L; l2 >= 0; l2--) {
-          t->m[l2] = V[l2 * T + ee];
+          t.m[l2] = V[l2 * T + ee];
           ee = PAR[l2 * T + ee];
         }
-        __threadfence();
-        *(volatile uint32_t *)&a.task_seq[base + lane] = 1u;
+        publish_task(a, base + lane, t);
       }
       __syncwarp();
       if (lane == 0) H->tot[L] = s2;
@@ -830,5 +847,7 @@ int gm_dfs(const MatchArgs &a, int num_sms, cudaStream_t s) {
   k_dfs<<<num_sms * per_sm, wpb * 32, smem, s>>>(a);
   GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
+  GM_CUDA(cudaMemcpyAsync(&a.st->tasks_donated, a.sched + GM_SCHED_RESERVE, sizeof(uint32_t),
+                          cudaMemcpyDeviceToDevice, s));
   return GAMMA_OK;
 }

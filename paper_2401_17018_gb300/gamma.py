@@ -43,7 +43,7 @@ class gamma_stats(ctypes.Structure):
                 ("work_items", ctypes.c_int64), ("touched", ctypes.c_int64), ("pool_used", ctypes.c_int64),
                 ("pool_cap", ctypes.c_int64), ("live_edges", ctypes.c_int64), ("expansions", ctypes.c_uint64),
                 ("alg_bytes", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
-                ("graph_captures", ctypes.c_int64)]
+                ("graph_captures", ctypes.c_int64), ("donated_tasks", ctypes.c_int64)]
 
 
 class gamma_server_options(ctypes.Structure):
