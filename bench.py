@@ -103,7 +103,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             p = [x.strip() for x in ln.split(",")]
@@ -112,13 +112,32 @@ class ClockSampler:
             try:
                 sm.append(float(p[1]))
                 mx.append(float(p[2]))
+                pw.append(float(p[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, p[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(pw) if pw else None,
+                "other_gpu_processes": other_processes(self.device)}
+
+
+def other_processes(device):
+    """Compute processes on the device other than this one (contention evidence)."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(device), "--query-compute-apps=pid,process_name,used_memory",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20).stdout
+    except (OSError, subprocess.SubprocessError):
+        return None
+    me = os.getpid()
+    rows = []
+    for ln in out.splitlines():
+        p = [x.strip() for x in ln.split(",")]
+        if len(p) >= 3 and p[0].isdigit() and int(p[0]) != me:
+            rows.append({"pid": int(p[0]), "name": p[1], "mib": p[2]})
+    return rows
 
 
 def measured_peaks():
@@ -324,7 +343,7 @@ def main():
         "data": "synthetic", "config": config_of(args.workload, b, len(queries)),
         "matches_per_s": world * sum(matches) / tot_s,
         "incremental_matches_per_step": matches[0],
-        "p50_ms": statistics.median(ms), "p99_ms": float(np.percentile(ms, 99)),
+        "p50_ms": statistics.median(ms), "p99_ms": float(np.percentile(ms, 99)), "step_ms": [round(x, 3) for x in ms],
         "phase_ms": phase_ms, "wall_s": wall,
         "e2e": {"value": e2e_v, "unit": "updates/s", "h2d_bytes_per_step": 9 * b,
                 "d2h_bytes_per_step": 16 * len(queries) + 3 * STATUS_BYTES},
