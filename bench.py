@@ -230,6 +230,205 @@ def config_of(workload, b, nq):
         "step": "apply batch (stage+seed+DFS+counts to host) + commit; batch and inverse alternate"}
 
 
+def run_batched(args):
+    """Batched form (A7): the same batch and 64 queries of 4..12 vertices,
+    (1) plain: one seed + DFS launch sequence per query, (2) batched: one
+    launch over all queries' seeds, autotuned and replayed as a CUDA graph.
+    Both must give identical counts."""
+    import torch
+    from paper_2401_17018_gb300 import gamma as G
+    from paper_2401_17018_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    w = I.make_workload("mid")
+    with open(os.path.join(ROOT, "tests/golden/queries_batched.json")) as f:
+        qd = json.load(f)
+    if qd.get("graph_digest") not in (None, w.graph.digest()):
+        raise SystemExit("stored queries were chosen on a different graph")
+    queries = [I.Query.from_json(x) for x in qd["queries"]]
+    batch = I.workload_batch(w, 90_000, 10_000)
+    inv = batch.inverse()
+    g = w.graph
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d_b = (dev(batch.op), dev(batch.src), dev(batch.dst))
+    d_i = (dev(inv.op), dev(batch.src), dev(batch.dst))
+    grid = [(wpb, t, gr) for wpb in (4, 8, 16) for t in (32, 64, 128, 256, 512) for gr in (1, 2, 4, 8, 16)]
+    if not args.full_grid:
+        grid = [(wpb, t, gr) for wpb in (4, 8, 16) for t in (32, 64, 128) for gr in (4, 16)]
+    out = {}
+    counts = {}
+    for form, flags in (("plain", G.GAMMA_F_PER_QUERY), ("batched", G.GAMMA_F_GRAPH)):
+        stream = torch.cuda.Stream()
+        ctx = G.Context(stream=stream, flags=flags)
+        ctx.load_graph(g.n, dev(g.labels), dev(g.src), dev(g.dst))
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
+        tuned = None
+        if form == "batched":
+            ctx.apply_batch(*d_b, qids)
+            tuned, sweep = G.gamma_autotune(ctx.h, grid, repeats=1)
+            ctx.commit()
+            ctx.apply_batch(*d_i, qids)
+            ctx.commit()
+        applied = 0
+        for k in range(args.warmup):
+            ctx.apply_batch(*(d_b if applied % 2 == 0 else d_i), qids)
+            ctx.commit()
+            applied += 1
+        if applied % 2:
+            ctx.apply_batch(*d_i, qids)
+            ctx.commit()
+            applied += 1
+        ms, res = [], []
+        launches0 = ctx.stats()["kernel_launches"]
+        for k in range(args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pos, neg = ctx.apply_batch(*(d_b if applied % 2 == 0 else d_i), qids)
+            ctx.commit()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            if applied % 2 == 0:
+                res.append((pos.tolist(), neg.tolist()))
+            applied += 1
+        st = ctx.stats()
+        out[form] = {"updates_per_s": len(batch) * len(ms) / (sum(ms) / 1e3), "ms_per_step": sum(ms) / len(ms),
+                     "p50_ms": statistics.median(ms), "p99_ms": float(np.percentile(ms, 99)),
+                     "gpu_launches_per_step": (st["kernel_launches"] - launches0) / len(ms),
+                     "graph_captures": st["graph_captures"]}
+        if tuned:
+            out[form]["tuned"] = tuned
+            out[form]["sweep"] = sweep
+        counts[form] = res[0] if res else None
+        ctx.close()
+    same = counts["plain"] == counts["batched"]
+    line = {"metric": "batched vs plain per-query launches: updates/s and p99 batch latency (1 GB300)",
+            "mode": "batched", "config": {"workload": "batched: R-MAT scale 20, %d queries of 4..12 vertices, "
+                                                      "batch 100000 (90000 ins + 10000 del)" % len(queries)},
+            "steps": args.steps, "warmup": args.warmup, "identical_counts": same,
+            "incremental_matches_per_step": int(sum(counts["plain"][0]) + sum(counts["plain"][1])) if counts["plain"] else None,
+            "plain": out["plain"], "batched": out["batched"],
+            "speedup": out["batched"]["updates_per_s"] / out["plain"]["updates_per_s"]}
+    print(json.dumps(line), flush=True)
+    if not same:
+        raise SystemExit("batched and plain forms disagree")
+
+
+def served_stream(w, n_batches, seed):
+    """Batches of floor(10^U(3, 6)) updates, insertions : deletions = 1 : 1.
+    Deletions are drawn from the current graph and insertions from the free
+    pool (held-out edges and edges deleted before), so each batch is valid
+    after the previous ones; order inside a batch is a seeded shuffle."""
+    from paper_2401_17018_gb300 import inputs as I
+    g = w.graph
+    src = np.concatenate([g.src, w.pool_src])
+    dst = np.concatenate([g.dst, w.pool_dst])
+    present = np.zeros(src.size, bool)
+    present[:g.src.size] = True
+    sizes = I.served_sizes(n_batches, seed)
+    out = []
+    for k, n in enumerate(sizes):
+        nd = int(n) // 2
+        ni = int(n) - nd
+        pres = np.flatnonzero(present)
+        free = np.flatnonzero(~present)
+        d = pres[np.argsort(I.rand_u64(seed, 31, np.arange(pres.size, dtype=np.uint64), k), kind="stable")[:nd]]
+        i = free[np.argsort(I.rand_u64(seed, 32, np.arange(free.size, dtype=np.uint64), k), kind="stable")[:ni]]
+        present[d] = False
+        present[i] = True
+        op = np.concatenate([np.ones(i.size, np.int8), -np.ones(d.size, np.int8)])
+        e = np.concatenate([i, d])
+        mix = I.shuffle_order(op.size, seed, 33, k)
+        out.append(I.Batch(op[mix], src[e][mix].astype(np.int32), dst[e][mix].astype(np.int32)))
+    return out
+
+
+def run_served(args):
+    """Served form (A7): a stream of uneven batches arriving as a Poisson
+    process at a fraction of the closed-loop capacity; one request at a time
+    ("plain") vs continuous batching ("served"); latency from arrival."""
+    import threading as th
+    import torch
+    from paper_2401_17018_gb300 import gamma as G
+    from paper_2401_17018_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    w = I.make_workload("served")
+    with open(os.path.join(ROOT, "tests/golden/queries_served.json")) as f:
+        qd = json.load(f)
+    if qd.get("graph_digest") not in (None, w.graph.digest()):
+        raise SystemExit("stored queries were chosen on a different graph")
+    queries = [I.Query.from_json(x) for x in qd["queries"]]
+    stream_b = served_stream(w, args.batches, w.seed)
+    total = sum(len(b) for b in stream_b)
+    g = w.graph
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d_graph = (dev(g.labels), dev(g.src), dev(g.dst))
+    ctx = G.Context(stream=torch.cuda.Stream())
+
+    def fresh():
+        ctx.load_graph(g.n, *d_graph)
+        return [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
+
+    # closed-loop capacity: every batch applied and committed back to back
+    qids = fresh()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for b in stream_b:
+        ctx.apply_batch(b.op, b.src, b.dst, qids)
+        ctx.commit()
+    cap = total / (time.perf_counter() - t)
+    mean_b = total / len(stream_b)
+    runs = {}
+    for load in args.loads:
+        gaps = I.poisson_gaps(len(stream_b), w.seed + int(load * 1000), load * cap / mean_b)
+        arrive = np.cumsum(gaps)
+        per_form = {}
+        for form, maxreq in (("plain", 1), ("served", 64)):
+            qids = fresh()
+            srv = G.Server(ctx, qids, max_requests=maxreq)
+            tickets = [None] * len(stream_b)
+            t0 = time.perf_counter()
+
+            def submit():
+                for k, b in enumerate(stream_b):
+                    dt = arrive[k] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                    tickets[k] = srv.submit(b.op, b.src, b.dst)
+
+            th_sub = th.Thread(target=submit)
+            th_sub.start()
+            th_sub.join()
+            res, lat, groups, first, last = [], [], [], None, None
+            for k in range(len(stream_b)):
+                rc, pos, neg, info = srv.wait(tickets[k])
+                if rc != G.GAMMA_OK:
+                    raise SystemExit("request %d failed with %d" % (k, rc))
+                res.append((pos.tolist(), neg.tolist()))
+                lat.append(info["done_ms"] - info["arrival_ms"])
+                groups.append(info["group_size"])
+                first = info["arrival_ms"] if first is None else min(first, info["arrival_ms"])
+                last = info["done_ms"] if last is None else max(last, info["done_ms"])
+            sst = srv.stats()
+            srv.stop()
+            per_form[form] = {"p50_ms": statistics.median(lat), "p99_ms": float(np.percentile(lat, 99)),
+                              "mean_ms": float(np.mean(lat)),
+                              "sustained_updates_per_s": total / ((last - first) / 1e3),
+                              "groups": sst["groups"], "max_group": sst["max_group"], "_res": res}
+        same = per_form["plain"].pop("_res") == per_form["served"].pop("_res")
+        if not same:
+            raise SystemExit("served results differ from one-at-a-time results at load %.2f" % load)
+        runs["%.2f" % load] = dict(per_form, identical_counts=same)
+    line = {"metric": "served form: p50/p99 batch latency from arrival and sustained updates/s (1 GB300)",
+            "mode": "served",
+            "config": {"workload": "served: R-MAT scale 22, %d queries of 6..8 vertices, %d batches of "
+                                   "floor(10^U(3,6)) updates (ins:del 1:1), Poisson arrivals" % (
+                                       len(queries), len(stream_b)), "updates": total},
+            "closed_loop_capacity_updates_per_s": cap, "loads": runs}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -239,9 +438,19 @@ def main():
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-query", action="store_true", help="plain form: one launch sequence per query")
+    ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
+                    help="plain: the metric's workload; batched / served: the A7 comparisons")
+    ap.add_argument("--full-grid", action="store_true", help="batched mode: sweep the whole autotuner grid")
+    ap.add_argument("--batches", type=int, default=30, help="served mode: batches in the stream")
+    ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 0.95],
+                    help="served mode: offered load as fractions of the closed-loop capacity")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batched":
+        return run_batched(args)
+    if args.mode == "served":
+        return run_served(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

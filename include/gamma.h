@@ -186,6 +186,21 @@ GAMMA_API int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out);
  * 0 keeps the current value for the three tuning fields). */
 GAMMA_API int gamma_set_options(gamma_ctx *ctx, const gamma_options *options);
 
+/* Autotuner for the batched form: one point of the search grid. */
+typedef struct {
+  int32_t warps_per_block;  /* 1..16 */
+  int32_t frontier_tile;    /* 32..4096 */
+  int32_t steal_grain;      /* >= 1 */
+  float ms;                 /* out: median seed + DFS time of the point (-1: not runnable) */
+} gamma_tune_point;
+
+/* Time the matching of the staged batch (seed + DFS, repeated `repeats` times)
+ * at every point of points[0..npoints) and keep the fastest point as the
+ * context's configuration (*best receives it, with its time).  The counts do
+ * not depend on the point.  GAMMA_ESTATE if no batch is staged. */
+GAMMA_API int gamma_autotune(gamma_ctx *ctx, int32_t npoints, gamma_tune_point *points, int32_t repeats,
+                             gamma_tune_point *best);
+
 /* Recount the staged batch without allocating anything: re-runs the DFS
  * kernel over the batch's work items (kept by the last gamma_apply_batch or
  * gamma_apply_batches) and writes the counts to host arrays out_pos / out_neg

@@ -239,6 +239,9 @@ static int make_order(srch *S, int32_t a, int32_t b) {
  *            rows; *n_tuples receives the number of rows produced
  *   node_budget: 0 = unlimited, else OR_EBUDGET once that many candidates were
  *            tried for one query
+ *   update_budget: 0 = none, else each (query, update) evaluation may try that
+ *            many candidates; one that needs more gets out_count = UINT64_MAX
+ *            ("not computed") and the next one starts afresh
  * Returns OR_OK, OR_EINVAL (bad_index = offending update), OR_EBUDGET, OR_ENOMEM.
  */
 int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
@@ -247,7 +250,7 @@ int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t
                       int64_t b, const int8_t *op, const int32_t *usrc, const int32_t *udst,
                       int64_t n_eval, const int64_t *eval_idx, uint64_t *out_count,
                       int32_t *tuples, int64_t tuple_cap, int64_t *n_tuples,
-                      uint64_t node_budget, int64_t *bad_index) {
+                      uint64_t node_budget, uint64_t update_budget, int64_t *bad_index) {
   if (bad_index) *bad_index = -1;
   if (n_tuples) *n_tuples = 0;
   if (nq < 0 || (tuples && nq != 1)) return OR_EINVAL;
@@ -315,6 +318,7 @@ int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t
       if (k < 0 || k >= b) { rc = OR_EINVAL; break; }
       S.sign = op[k]; S.upd = k; S.view = (op[k] == 1) ? &AP : &AG;
       S.count = 0;
+      if (update_budget) { S.nodes = 0; S.budget = update_budget; S.over_budget = 0; }
       for (int32_t e = 0; e < S.eq; e++) {
         for (int o = 0; o < 2; o++) {
           int32_t a = S.qs[e], bq = S.qd[e];
@@ -324,11 +328,11 @@ int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t
           memset(S.used_q, 0, sizeof(S.used_q));
           S.phi[a] = x; S.phi[bq] = y; S.used_q[a] = S.used_q[bq] = 1;
           extend(&S, 2);
-          if (S.over_budget) { rc = OR_EBUDGET; break; }
+          if (S.over_budget) { if (!update_budget) rc = OR_EBUDGET; break; }
         }
-        if (rc != OR_OK) break;
+        if (rc != OR_OK || S.over_budget) break;
       }
-      if (out_count) out_count[(int64_t)j * ne + i] = S.count;
+      if (out_count) out_count[(int64_t)j * ne + i] = (update_budget && S.over_budget) ? UINT64_MAX : S.count;
     }
   }
   adj_free(&AG); adj_free(&AP);
@@ -345,6 +349,6 @@ int oracle_bdsm(int32_t n, const int32_t *labels, int64_t m, const int32_t *src,
                 uint64_t node_budget, int64_t *bad_index) {
   int64_t zero = 0;
   return oracle_bdsm_multi(n, labels, m, src, dst, 1, &q, qlabels, &zero, &eq, qsrc, qdst, &zero, b, op, usrc,
-                           udst, n_eval, eval_idx, out_count, tuples, tuple_cap, n_tuples, node_budget,
+                           udst, n_eval, eval_idx, out_count, tuples, tuple_cap, n_tuples, node_budget, 0,
                            bad_index);
 }

@@ -73,7 +73,7 @@ def _load():
             ctypes.c_int64, p, p, p,
             ctypes.c_int64, p, p,
             p, ctypes.c_int64, p,
-            ctypes.c_uint64, p]
+            ctypes.c_uint64, ctypes.c_uint64, p]
         _lib = lib
     return _lib
 
@@ -132,10 +132,15 @@ def bdsm(n: int, labels, src, dst, query, batch, eval_idx: Optional[Sequence[int
     return counts, tup
 
 
+NOT_COMPUTED = np.iinfo(np.uint64).max
+
+
 def bdsm_multi(n: int, labels, src, dst, queries, batch, eval_idx: Optional[Sequence[int]] = None,
-               budget: int = 0) -> np.ndarray:
+               budget: int = 0, update_budget: int = 0) -> np.ndarray:
     """O2 for several queries in one call (G, G' and the batch map are built
-    once). Returns counts[j, i] = matches of query j charged to update eval_idx[i]."""
+    once). Returns counts[j, i] = matches of query j charged to update eval_idx[i].
+    With update_budget, a (query, update) pair needing more candidate tests
+    than that is skipped and reported as NOT_COMPUTED."""
     lib = _load()
     labels = np.ascontiguousarray(labels, np.int32)
     src = np.ascontiguousarray(src, np.int32)
@@ -158,7 +163,7 @@ def bdsm_multi(n: int, labels, src, dst, queries, batch, eval_idx: Optional[Sequ
     rc = lib.oracle_bdsm_multi(n, _ptr(labels), src.size, _ptr(src), _ptr(dst),
                                len(queries), _ptr(qn), _ptr(ql), _ptr(lo), _ptr(qe), _ptr(qs), _ptr(qd), _ptr(eo),
                                b, _ptr(op), _ptr(us), _ptr(ud), ne, _ptr(ev), _ptr(counts),
-                               None, 0, None, budget, ctypes.byref(bad))
+                               None, 0, None, budget, update_budget, ctypes.byref(bad))
     if rc != OK:
         raise OracleError(rc, bad.value)
     return counts[:len(queries) * ne].reshape(len(queries), ne)

@@ -1017,6 +1017,47 @@ int gamma_fetch_matches(gamma_ctx *ctx, gamma_matches *out) {
   return GAMMA_OK;
 }
 
+int gamma_autotune(gamma_ctx *ctx, int32_t npoints, gamma_tune_point *points, int32_t repeats,
+                   gamma_tune_point *best) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->staged) return ctx->fail(GAMMA_ESTATE, "gamma_autotune: no staged batch");
+  if (npoints < 1 || !points || !best || repeats < 1) return ctx->fail(GAMMA_EINVAL, "gamma_autotune: bad arguments");
+  cudaSetDevice(ctx->device);
+  const int wpb0 = ctx->wpb, tile0 = ctx->tile, grain0 = ctx->grain;
+  int bi = -1;
+  for (int i = 0; i < npoints; i++) {
+    gamma_tune_point &pt = points[i];
+    pt.ms = -1.f;
+    if (pt.warps_per_block < 1 || pt.warps_per_block > 16 || pt.frontier_tile < 32 || pt.frontier_tile > 4096 ||
+        pt.steal_grain < 1)
+      continue;
+    ctx->wpb = pt.warps_per_block;
+    ctx->tile = pt.frontier_tile;
+    ctx->grain = pt.steal_grain;
+    std::vector<float> t;
+    bool ok = true;
+    for (int r = 0; r < repeats && ok; r++) {
+      int rc = run_match(ctx, nullptr, 0, 0);
+      if (rc || ctx->h_st->err) { ok = false; cudaGetLastError(); break; }
+      t.push_back((float)(ctx->stats.ms_seed + ctx->stats.ms_match));
+    }
+    if (!ok) continue;
+    std::sort(t.begin(), t.end());
+    pt.ms = t[t.size() / 2];
+    if (bi < 0 || pt.ms < points[bi].ms) bi = i;
+  }
+  if (bi < 0) {
+    ctx->wpb = wpb0; ctx->tile = tile0; ctx->grain = grain0;
+    return ctx->fail(GAMMA_EINVAL, "gamma_autotune: no point could run");
+  }
+  ctx->wpb = points[bi].warps_per_block;
+  ctx->tile = points[bi].frontier_tile;
+  ctx->grain = points[bi].steal_grain;
+  *best = points[bi];
+  return GAMMA_OK;
+}
+
 int gamma_update_counts(gamma_ctx *ctx, int32_t j, uint64_t *out) {
   if (!ctx) return GAMMA_EINVAL;
   ctx->err.clear();

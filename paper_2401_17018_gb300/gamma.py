@@ -60,6 +60,11 @@ class gamma_server_stats(ctypes.Structure):
                 ("max_group", ctypes.c_int64), ("busy_ms", ctypes.c_double)]
 
 
+class gamma_tune_point(ctypes.Structure):
+    _fields_ = [("warps_per_block", ctypes.c_int32), ("frontier_tile", ctypes.c_int32),
+                ("steal_grain", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
 class GammaError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("%s: %s" % (_NAMES.get(code, str(code)), msg))
@@ -84,6 +89,8 @@ _SIGS = {
     "gamma_set_options": (ctypes.c_int, [_P, ctypes.POINTER(gamma_options)]),
     "gamma_last_error": (ctypes.c_char_p, [_P]),
     "gamma_recount_noalloc": (ctypes.c_int, [_P, _P, _P]),
+    "gamma_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(gamma_tune_point), ctypes.c_int32,
+                                      ctypes.POINTER(gamma_tune_point)]),
     "gamma_server_start": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(gamma_server_options),
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "gamma_server_submit": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.POINTER(ctypes.c_int64)]),
@@ -336,6 +343,16 @@ class Context:
     def export_adjacency(self, n: int):
         st = self.stats()
         return gamma_export_adjacency(self.h, n, int(st["pool_used"]))
+
+
+def gamma_autotune(ctx: int, grid, repeats: int = 1):
+    """Sweep (warps_per_block, frontier_tile, steal_grain) points on the staged
+    batch; returns (best point as a dict, list of every point with its ms)."""
+    pts = (gamma_tune_point * len(grid))(*[gamma_tune_point(w, t, g, 0.0) for w, t, g in grid])
+    best = gamma_tune_point()
+    _check(ctx, load_library().gamma_autotune(ctx, len(grid), pts, int(repeats), ctypes.byref(best)))
+    as_dict = lambda p: {k: getattr(p, k) for k, _ in gamma_tune_point._fields_}
+    return as_dict(best), [as_dict(p) for p in pts]
 
 
 def gamma_recount_noalloc(ctx: int, nslots: int) -> Tuple[np.ndarray, np.ndarray]:

@@ -251,7 +251,8 @@ def random_walk_query(off: np.ndarray, nbr: np.ndarray, labels: np.ndarray, q: i
     of a uniformly drawn edge and repeatedly adds, among the neighbours of the
     vertices taken so far, one with the most neighbours inside the taken set
     (ties broken by the seeded generator), until ``q`` vertices are taken.
-    "dense" keeps the induced subgraph when its average degree is > 3.
+    "dense" keeps the induced subgraph when its average degree is > 3;
+    "dense_ge3" when it is >= 3 (the paper's Dense class, Sec. VI-A).
     "sparse" keeps a random spanning tree of the induced subgraph plus random
     further induced edges up to |E| = min(#induced, q + r) with r in
     [0, q/2] drawn per attempt, so the average degree is <= 3 and the query
@@ -314,8 +315,9 @@ def random_walk_query(off: np.ndarray, nbr: np.ndarray, labels: np.ndarray, q: i
             best = u[cnt == cnt.max()]
             order.append(int(best[draw() % best.size]))
         ind = induced(order)
-        if kind == "dense":
-            if not 2.0 * len(ind) / q > 3.0:
+        if kind in ("dense", "dense_ge3"):
+            avg = 2.0 * len(ind) / q
+            if not (avg > 3.0 if kind == "dense" else avg >= 3.0):
                 return None
             edges = ind
         else:

@@ -10,7 +10,7 @@ updates (every ``stride``-th update) within ``budget`` candidate tests, and
 the sample must contain at least one incremental match. Rejected candidates
 are logged in the output with the reason. Nothing here touches the CUDA path.
 
-Usage: python tests/golden/make_queries.py mid|batched [--workers 8]
+Usage: python tests/golden/make_queries.py mid|batched|served|large [--workers 8]
 """
 import argparse
 import json
@@ -31,14 +31,20 @@ from paper_2401_17018_gb300 import inputs as I  # noqa: E402
 SPECS = {
     # name: (workload, batch inserts, batch deletions, plan of (kind, q) per query)
     "mid": ("mid", 90_000, 10_000, [("sparse", 6)] * 10 + [("dense", 6)] * 10),
+    # 64 queries of 4..12 vertices (uneven sizes), alternating sparse and dense
     "batched": ("mid", 90_000, 10_000,
-                [("sparse" if i % 2 == 0 else "dense", 4 + (i * 7) % 9) for i in range(64)]),
+                [("sparse" if i % 2 == 0 else "dense_ge3", 4 + (i * 7) % 9) for i in range(64)]),
+    # 16 queries of 6..8 vertices on the scale-22 graph (the served stream's first batch)
+    "served": ("served", 3_000, 1_000, [("dense", 6 + i % 3) for i in range(16)]),
+    # 8-vertex queries, 4 sparse and 4 dense, on the scale-23 graph (first batch)
+    "large": ("large", 800_000, 200_000, [("sparse", 8)] * 4 + [("dense", 8)] * 4),
 }
 # (stride, budget) per query class: every stride-th update of the batch is
 # evaluated, within budget candidate tests. Sparse queries on the power-law
 # graphs are far costlier per update, so they get a thinner sample and a
 # larger budget.
-RULES = {"dense": (200, 10_000_000), "sparse": (2500, 40_000_000), "tree": (2500, 40_000_000)}
+RULES = {"dense": (200, 10_000_000), "dense_ge3": (200, 10_000_000), "sparse": (2500, 40_000_000),
+         "tree": (2500, 40_000_000)}
 
 _W = None
 

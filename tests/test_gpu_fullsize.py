@@ -1,0 +1,75 @@
+"""Parity at the benchmark's full sizes, on sampled outputs.
+
+At these sizes the oracle cannot enumerate everything, so the CUDA path is
+checked (a) on the per-update charged counts of a seeded sample of updates,
+which the oracle computes one by one (pairs that would need more than a fixed
+number of candidate tests are skipped, a rule that depends only on the oracle),
+and (b) on properties that hold at any size: totals are the sums of the
+per-update charges split by sign, and the inverse batch applied to G' swaps
+the positive and negative totals.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2401_17018_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2401_17018_gb300 import gamma
+    return gamma
+
+
+def _load_queries(name, w):
+    with open(os.path.join(GOLD, "queries_%s.json" % name)) as f:
+        d = json.load(f)
+    assert d["graph_digest"] == w.graph.digest()
+    return [I.Query.from_json(x) for x in d["queries"]]
+
+
+def _sample(b, k, seed):
+    return np.sort(np.argsort(I.rand_u64(seed, 77, np.arange(b, dtype=np.uint64)))[:k])
+
+
+def _check_workload(G, w, queries, batch, n_sample, update_budget, flags=0):
+    import torch
+    g = w.graph
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with G.Context(flags=flags | G.GAMMA_F_PER_UPDATE, stream=torch.cuda.Stream()) as ctx:
+        ctx.load_graph(g.n, dev(g.labels), dev(g.src), dev(g.dst))
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
+        pos, neg = ctx.apply_batch(dev(batch.op), dev(batch.src), dev(batch.dst), qids)
+        per = np.stack([ctx.update_counts(j) for j in range(len(qids))])
+        ctx.commit()
+        inv = batch.inverse()
+        pos2, neg2 = ctx.apply_batch(dev(inv.op), dev(batch.src), dev(batch.dst), qids)
+        ctx.commit()
+    ins = batch.op > 0
+    assert np.array_equal(per[:, ins].sum(axis=1), pos) and np.array_equal(per[:, ~ins].sum(axis=1), neg)
+    assert np.array_equal(pos2, neg) and np.array_equal(neg2, pos)
+    ev = _sample(len(batch), n_sample, 5)
+    want = O.bdsm_multi(g.n, g.labels, g.src, g.dst, queries, batch, eval_idx=ev, update_budget=update_budget)
+    done = want != O.NOT_COMPUTED
+    assert done.mean() >= 0.5, "the oracle finished too few sampled pairs"
+    got = per[:, ev]
+    assert np.array_equal(got[done], want[done])
+    return int(done.sum()), int(pos.sum() + neg.sum())
+
+
+def test_mid_workload_fullsize_sampled(G):
+    """The bench workload: scale-20 R-MAT, 20 six-vertex queries, 100k updates."""
+    w = I.make_workload("mid")
+    queries = _load_queries("mid", w)
+    batch = I.workload_batch(w, 90_000, 10_000)
+    checked, total = _check_workload(G, w, queries, batch, n_sample=32, update_budget=2_000_000)
+    assert checked >= 320 and total > 0

@@ -438,3 +438,20 @@ def test_server_results_equal_sequential(G):
         srv.stop()
     assert got == alone
     assert max(groups) > 1 and st["requests"] == len(reqs) and st["groups"] < len(reqs)
+
+
+def test_autotune_picks_a_point_and_keeps_counts(G):
+    w = I.make_workload("tiny")
+    b = I.workload_batch(w, 400, 100, sub=6)
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)])]
+    with G.Context() as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        pos, neg = ctx.apply_batch(b.op, b.src, b.dst, qids)
+        grid = [(4, 32, 1), (8, 64, 16), (16, 128, 4), (0, 64, 4)]  # the last point is invalid
+        best, pts = G.gamma_autotune(ctx.h, grid, repeats=2)
+        assert pts[-1]["ms"] < 0 and all(p["ms"] >= 0 for p in pts[:-1])
+        assert best["ms"] == min(p["ms"] for p in pts[:-1])
+        p2, n2 = G.gamma_recount_noalloc(ctx.h, len(qids))
+        assert np.array_equal(p2, pos) and np.array_equal(n2, neg)
+        ctx.commit()
