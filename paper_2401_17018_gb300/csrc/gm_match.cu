@@ -350,7 +350,10 @@ __device__ __forceinline__ uint32_t demand(const MatchArgs &a) {
   return d > 0 ? (uint32_t)d : 0u;
 }
 
-__global__ void k_dfs(MatchArgs a) {
+// 64 registers a thread: 32 resident warps per SM at any block size (the
+// uncapped build needs 72 and fits only 24 warps of 256-thread blocks, 15%
+// slower on the mid workload; caps of 56 and 48 spill without gaining)
+__global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const GraphDev &g = a.g;
   GmStatus *st = a.st;
