@@ -59,6 +59,8 @@ RULES = {"dense": (200, 10_000_000), "dense_ge3": (200, 10_000_000), "sparse": (
 SAMPLING = {
     "batched": {"rules": {"dense_ge3": (5000, 20_000_000), "sparse": (5000, 40_000_000)},
                 "heavy": 8, "max_attempts": 240},
+    "large": {"rules": {"dense": (20000, 20_000_000), "sparse": (20000, 40_000_000)},
+              "heavy": 8, "max_attempts": 120},
 }
 DEFAULT_SAMPLING = {"rules": RULES, "heavy": 0, "max_attempts": 20000}
 
