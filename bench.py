@@ -330,35 +330,6 @@ def run_batched(args):
         raise SystemExit("batched and plain forms disagree")
 
 
-def served_stream(w, n_batches, seed):
-    """Batches of floor(10^U(3, 6)) updates, insertions : deletions = 1 : 1.
-    Deletions are drawn from the current graph and insertions from the free
-    pool (held-out edges and edges deleted before), so each batch is valid
-    after the previous ones; order inside a batch is a seeded shuffle."""
-    from paper_2401_17018_gb300 import inputs as I
-    g = w.graph
-    src = np.concatenate([g.src, w.pool_src])
-    dst = np.concatenate([g.dst, w.pool_dst])
-    present = np.zeros(src.size, bool)
-    present[:g.src.size] = True
-    sizes = I.served_sizes(n_batches, seed)
-    out = []
-    for k, n in enumerate(sizes):
-        nd = int(n) // 2
-        ni = int(n) - nd
-        pres = np.flatnonzero(present)
-        free = np.flatnonzero(~present)
-        d = pres[np.argsort(I.rand_u64(seed, 31, np.arange(pres.size, dtype=np.uint64), k), kind="stable")[:nd]]
-        i = free[np.argsort(I.rand_u64(seed, 32, np.arange(free.size, dtype=np.uint64), k), kind="stable")[:ni]]
-        present[d] = False
-        present[i] = True
-        op = np.concatenate([np.ones(i.size, np.int8), -np.ones(d.size, np.int8)])
-        e = np.concatenate([i, d])
-        mix = I.shuffle_order(op.size, seed, 33, k)
-        out.append(I.Batch(op[mix], src[e][mix].astype(np.int32), dst[e][mix].astype(np.int32)))
-    return out
-
-
 def run_served(args):
     """Served form (A7): a stream of uneven batches arriving as a Poisson
     process at a fraction of the closed-loop capacity; one request at a time
@@ -374,7 +345,7 @@ def run_served(args):
     if qd.get("graph_digest") not in (None, w.graph.digest()):
         raise SystemExit("stored queries were chosen on a different graph")
     queries = [I.Query.from_json(x) for x in qd["queries"]]
-    stream_b = served_stream(w, args.batches, w.seed)
+    stream_b = I.served_stream(w, args.batches, w.seed)
     total = sum(len(b) for b in stream_b)
     g = w.graph
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()

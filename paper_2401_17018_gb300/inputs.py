@@ -31,6 +31,7 @@ _M2 = U64(0x94D049BB133111EB)
 # stream identifiers (arbitrary distinct constants)
 S_RMAT, S_PERM, S_LABEL, S_SHUF, S_DEL, S_MIX, S_QUERY, S_SIZE, S_ARRIVE = (
     11, 12, 13, 14, 15, 16, 17, 18, 19)
+S_SRV_DEL, S_SRV_INS, S_SRV_MIX = 31, 32, 33
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -411,6 +412,53 @@ def served_sizes(n_batches: int, seed: int, lo_exp: float = 3.0, hi_exp: float =
     """Batch sizes floor(10^U(lo, hi)), U drawn from 32-bit integers."""
     r = rand_u32(seed, S_SIZE, np.arange(n_batches, dtype=U64)).astype(np.float64) / float(1 << 32)
     return np.floor(10.0 ** (lo_exp + (hi_exp - lo_exp) * r)).astype(np.int64)
+
+
+def sample_distinct(n: int, k: int, seed: int, stream: int, sub: int = 0) -> np.ndarray:
+    """k distinct uniform draws from range(n), in draw order: counter-based
+    draws modulo n, repeats skipped (so the result is a uniform sample
+    without replacement; the modulo bias is below n / 2^64)."""
+    if k > n:
+        raise ValueError("cannot draw %d distinct values from %d" % (k, n))
+    got = np.empty(0, np.int64)
+    ctr = 0
+    while got.size < k:
+        m = max(2 * (k - got.size), 1024)
+        r = (rand_u64(seed, stream, np.arange(ctr, ctr + m, dtype=U64), sub) % U64(n)).astype(np.int64)
+        ctr += m
+        cand = np.concatenate([got, r])
+        _, first = np.unique(cand, return_index=True)
+        got = cand[np.sort(first)][:k]
+    return got
+
+
+def served_stream(w: "Workload", n_batches: int, seed: int, lo_exp: float = 3.0,
+                  hi_exp: float = 6.0) -> List[Batch]:
+    """The served workload's request stream: batches of floor(10^U(3, 6))
+    updates (the exponents are parameters) with insertions : deletions = 1 : 1.  Deletions are drawn from the
+    graph as it stands after the previous batches, insertions from the free
+    pool (held-out edges and edges deleted earlier), so every batch is valid
+    in order; the updates of a batch are interleaved by a seeded shuffle."""
+    g = w.graph
+    src = np.concatenate([g.src, w.pool_src])
+    dst = np.concatenate([g.dst, w.pool_dst])
+    present = np.zeros(src.size, bool)
+    present[:g.src.size] = True
+    out = []
+    for k, n in enumerate(served_sizes(n_batches, seed, lo_exp, hi_exp)):
+        nd = int(n) // 2
+        ni = int(n) - nd
+        pres = np.flatnonzero(present)
+        free = np.flatnonzero(~present)
+        d = pres[sample_distinct(pres.size, nd, seed, S_SRV_DEL, k)]
+        i = free[sample_distinct(free.size, ni, seed, S_SRV_INS, k)]
+        present[d] = False
+        present[i] = True
+        op = np.concatenate([np.ones(i.size, np.int8), -np.ones(d.size, np.int8)])
+        e = np.concatenate([i, d])
+        mix = shuffle_order(op.size, seed, S_SRV_MIX, k)
+        out.append(Batch(op[mix], src[e][mix].astype(np.int32), dst[e][mix].astype(np.int32)))
+    return out
 
 
 def poisson_gaps(n: int, seed: int, rate_per_s: float) -> np.ndarray:

@@ -73,3 +73,64 @@ def test_mid_workload_fullsize_sampled(G):
     batch = I.workload_batch(w, 90_000, 10_000)
     checked, total = _check_workload(G, w, queries, batch, n_sample=32, update_budget=2_000_000)
     assert checked >= 320 and total > 0
+
+
+def test_batched_workload_fullsize_sampled(G):
+    """The batched workload: the mid graph and batch with 64 queries of 4..8
+    vertices, in the batched form replayed as a CUDA graph."""
+    w = I.make_workload("mid")
+    queries = _load_queries("batched", w)
+    assert len(queries) == 64
+    batch = I.workload_batch(w, 90_000, 10_000)
+    checked, total = _check_workload(G, w, queries, batch, n_sample=8, update_budget=1_000_000,
+                                     flags=G.GAMMA_F_GRAPH)
+    assert checked >= 256 and total > 0
+
+
+def test_served_workload_fullsize_sampled(G):
+    """The served workload: the first three requests of the served stream on
+    the scale-22 graph.  Through the server each request gets the counts of
+    applying the requests one after another; those equal the sums of the
+    per-update charges, which the oracle checks on sampled updates against
+    the graph each request meets."""
+    import torch
+    w = I.make_workload("served")
+    queries = _load_queries("served", w)
+    stream = I.served_stream(w, 3, w.seed)
+    g = w.graph
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    alone, per = [], []
+    with G.Context(flags=G.GAMMA_F_PER_UPDATE) as ctx:
+        ctx.load_graph(g.n, dev(g.labels), dev(g.src), dev(g.dst))
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
+        for b in stream:
+            pos, neg = ctx.apply_batch(dev(b.op), dev(b.src), dev(b.dst), qids)
+            per.append(np.stack([ctx.update_counts(j) for j in range(len(qids))]))
+            alone.append((pos.tolist(), neg.tolist()))
+            ctx.commit()
+    with G.Context() as ctx:
+        ctx.load_graph(g.n, dev(g.labels), dev(g.src), dev(g.dst))
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
+        srv = G.Server(ctx, qids, max_requests=8)
+        tickets = [srv.submit(b.op, b.src, b.dst) for b in stream]
+        served = []
+        for t in tickets:
+            rc, pos, neg, info = srv.wait(t)
+            assert rc == G.GAMMA_OK
+            served.append((pos.tolist(), neg.tolist()))
+        srv.stop()
+    assert served == alone
+    cur = (g.src, g.dst)
+    checked = 0
+    for k, b in enumerate(stream):
+        ins = b.op > 0
+        assert per[k][:, ins].sum(axis=1).tolist() == alone[k][0]
+        assert per[k][:, ~ins].sum(axis=1).tolist() == alone[k][1]
+        ev = _sample(len(b), 8, 11 + k)
+        want = O.bdsm_multi(g.n, g.labels, cur[0], cur[1], queries, b, eval_idx=ev, update_budget=2_000_000)
+        done = want != O.NOT_COMPUTED
+        assert done.mean() >= 0.5
+        assert np.array_equal(per[k][:, ev][done], want[done])
+        checked += int(done.sum())
+        cur = I.apply_batch_edges(cur[0], cur[1], b)
+    assert checked >= 3 * 8 * 16 // 2
