@@ -52,6 +52,10 @@ WORKLOADS = {
 }
 METRIC = "updates/s & incremental matches/s per batch (1 GB300); p50/p99 batch latency"
 STATUS_BYTES = 112  # the library's status block, read back after staging, matching and commit
+# batched / served modes: a bound on one apply's DFS work (32-wide expansion
+# steps, about a minute of GPU time), so a workload heavier than intended
+# fails with GAMMA_ETIMEOUT instead of running on
+WORK_BUDGET = 100_000_000_000
 
 
 def load_workload(name):
@@ -247,7 +251,7 @@ def config_of(workload, b, nq):
 
 
 def run_batched(args):
-    """Batched form (A7): the same batch and 64 queries of 4..12 vertices,
+    """Batched form (A7): the same batch and the 64 stored batched queries,
     (1) plain: one seed + DFS launch sequence per query, (2) batched: one
     launch over all queries' seeds, autotuned and replayed as a CUDA graph.
     Both must give identical counts."""
@@ -269,12 +273,12 @@ def run_batched(args):
     d_i = (dev(inv.op), dev(batch.src), dev(batch.dst))
     grid = [(wpb, t, gr) for wpb in (4, 8, 16) for t in (32, 64, 128, 256, 512) for gr in (1, 2, 4, 8, 16)]
     if not args.full_grid:
-        grid = [(wpb, t, gr) for wpb in (4, 8, 16) for t in (32, 64, 128) for gr in (4, 16)]
+        grid = [(wpb, t, gr) for wpb in (4, 8, 16) for t in (64, 128) for gr in (4, 16)]
     out = {}
     counts = {}
     for form, flags in (("plain", G.GAMMA_F_PER_QUERY), ("batched", G.GAMMA_F_GRAPH)):
         stream = torch.cuda.Stream()
-        ctx = G.Context(stream=stream, flags=flags)
+        ctx = G.Context(stream=stream, flags=flags, work_budget=WORK_BUDGET)
         ctx.load_graph(g.n, dev(g.labels), dev(g.src), dev(g.dst))
         qids = [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
         tuned = None
@@ -319,8 +323,10 @@ def run_batched(args):
         ctx.close()
     same = counts["plain"] == counts["batched"]
     line = {"metric": "batched vs plain per-query launches: updates/s and p99 batch latency (1 GB300)",
-            "mode": "batched", "config": {"workload": "batched: R-MAT scale 20, %d queries of 4..12 vertices, "
-                                                      "batch 100000 (90000 ins + 10000 del)" % len(queries)},
+            "mode": "batched", "config": {"workload": "batched: R-MAT scale 20, %d queries of %d..%d vertices "
+                                                      "(sparse and dense alternating), batch 100000 (90000 ins + "
+                                                      "10000 del)" % (len(queries), min(q.labels.size for q in queries),
+                                                                      max(q.labels.size for q in queries))},
             "steps": args.steps, "warmup": args.warmup, "identical_counts": same,
             "incremental_matches_per_step": int(sum(counts["plain"][0]) + sum(counts["plain"][1])) if counts["plain"] else None,
             "plain": out["plain"], "batched": out["batched"],
@@ -350,7 +356,7 @@ def run_served(args):
     g = w.graph
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     d_graph = (dev(g.labels), dev(g.src), dev(g.dst))
-    ctx = G.Context(stream=torch.cuda.Stream())
+    ctx = G.Context(stream=torch.cuda.Stream(), work_budget=WORK_BUDGET)
 
     def fresh():
         ctx.load_graph(g.n, *d_graph)

@@ -53,6 +53,16 @@ __device__ __forceinline__ bool tag_ok(uint32_t t, uint32_t sdel, uint32_t upd, 
 
 // is the edge (w, c) visible in the seed's view under the charging rule?
 // x = adjacency key of c (flag bit ignored)
+// Algorithmic-byte accumulator: counts only in the instrumented build of the
+// DFS kernel (C = true); in the timed build every update compiles away.
+template <bool C>
+struct ByteCount {
+  uint64_t v = 0;
+  __device__ __forceinline__ void operator+=(uint64_t x) {
+    if (C) v += x;
+  }
+};
+
 // algorithmic bytes of one binary search over a list of d entries: one 32-B
 // sector per halving step, never more than the whole list
 __device__ __forceinline__ uint32_t probe_bytes(uint32_t d) {
@@ -60,8 +70,9 @@ __device__ __forceinline__ uint32_t probe_bytes(uint32_t d) {
   return min(4u * d, 32u * steps) + 8u;
 }
 
+template <bool C>
 __device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t x, uint32_t sdel,
-                                        uint32_t upd, const uint32_t *req, uint32_t r, uint64_t &bytes) {
+                                        uint32_t upd, const uint32_t *req, uint32_t r, ByteCount<C> &bytes) {
   const uint32_t key = x & ~1u;
   const int32_t h = __ldg(g.hub_id + w);
   if (h >= 0) {
@@ -115,8 +126,9 @@ __device__ __forceinline__ void seg_bounds(const GraphDev &g, const uint32_t *L,
 // absolute col slot and length of N^lab(v): from the hub offset table, else
 // from the prefix of v's per-label counts when none of them is saturated,
 // else by binary search
+template <bool C>
 __device__ __forceinline__ void label_segment(const GraphDev &g, uint32_t v, int lab, uint32_t &lo,
-                                              uint32_t &len, uint64_t &bytes) {
+                                              uint32_t &len, ByteCount<C> &bytes) {
   const uint2 a = __ldg(reinterpret_cast<const uint2 *>(g.adj) + v);
   const int32_t h = __ldg(g.hub_id + v);
   bytes += 12;
@@ -217,7 +229,7 @@ __global__ void k_seed(MatchArgs a) {
         const uint16_t bw = P.bwd[2];
         uint32_t best_len = 0xffffffffu, best_lo = 0;
         int drv = 0;
-        uint64_t nb = 0;
+        ByteCount<false> nb;
         for (int pos = 0; pos < 2; pos++) {
           if (!((bw >> pos) & 1)) continue;
           uint32_t lo, len;
@@ -353,6 +365,7 @@ __device__ __forceinline__ uint32_t demand(const MatchArgs &a) {
 // 64 registers a thread: 32 resident warps per SM at any block size (the
 // uncapped build needs 72 and fits only 24 warps of 256-thread blocks, 15%
 // slower on the mid workload; caps of 56 and 48 spill without gaining)
+template <bool kCountBytes>
 __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const GraphDev &g = a.g;
@@ -470,7 +483,7 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
     const uint32_t sdel = a.op[upd] < 0 ? 1u : 0u;
     const uint32_t rq = a.req ? __ldg(a.req + upd) : 0u;
     uint64_t wcount = 0;
-    uint64_t lbytes = 0;  // this lane's algorithmic bytes (only reported with count_bytes)
+    ByteCount<kCountBytes> lbytes;  // this lane's algorithmic bytes (instrumented build only)
     uint32_t chunks = 0;
 
     // prepare level L (position L+2): driver segment of every entry for position L+3
@@ -797,10 +810,10 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       }
       if ((chunks & 1023u) == 0 && warp_read(&st->abort)) break;
     }
-    if (a.count_bytes) {
-      lbytes += (lane == 0) ? 16u : 0u;
-      for (int d = 16; d > 0; d >>= 1) lbytes += __shfl_down_sync(GM_FULL, lbytes, d);
-      if (lane == 0) atomicAdd((unsigned long long *)&st->alg_bytes, (unsigned long long)lbytes);
+    if (kCountBytes) {
+      uint64_t tb = lbytes.v + ((lane == 0) ? 16u : 0u);
+      for (int d = 16; d > 0; d >>= 1) tb += __shfl_down_sync(GM_FULL, tb, d);
+      if (lane == 0) atomicAdd((unsigned long long *)&st->alg_bytes, (unsigned long long)tb);
     }
     if (lane == 0) {
       if (wcount) {
@@ -835,22 +848,27 @@ int gm_seed(const MatchArgs &a, cudaStream_t s) {
   return GAMMA_OK;
 }
 
-int gm_dfs(const MatchArgs &a, int num_sms, cudaStream_t s) {
+template <bool kCountBytes>
+static int launch_dfs(const MatchArgs &a, int num_sms, cudaStream_t s) {
   const int wpb = a.warps_per_block;
   const size_t smem = smem_per_warp(a.tile, a.nlev) * wpb;
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
-    GM_CUDA(cudaFuncSetAttribute(k_dfs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GM_CUDA(cudaFuncSetAttribute(k_dfs<kCountBytes>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = smem;
   }
   int per_sm = 0;
-  GM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfs, wpb * 32, smem));
+  GM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfs<kCountBytes>, wpb * 32, smem));
   if (per_sm < 1) return GAMMA_EINVAL;
   GM_CUDA(cudaMemsetAsync(a.sched, 0, GM_SCHED_WORDS * sizeof(uint32_t), s));
-  k_dfs<<<num_sms * per_sm, wpb * 32, smem, s>>>(a);
+  k_dfs<kCountBytes><<<num_sms * per_sm, wpb * 32, smem, s>>>(a);
   GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   GM_CUDA(cudaMemcpyAsync(&a.st->tasks_donated, a.sched + GM_SCHED_RESERVE, sizeof(uint32_t),
                           cudaMemcpyDeviceToDevice, s));
   return GAMMA_OK;
+}
+
+int gm_dfs(const MatchArgs &a, int num_sms, cudaStream_t s) {
+  return a.count_bytes ? launch_dfs<true>(a, num_sms, s) : launch_dfs<false>(a, num_sms, s);
 }

@@ -54,13 +54,14 @@ RULES = {"dense": (200, 10_000_000), "dense_ge3": (200, 10_000_000), "sparse": (
          "tree": (2500, 40_000_000)}
 
 # per-workload sampling that differs from the defaults above: (stride, budget)
-# per class, the heavy updates added to the sample, and the attempt cap per
-# (class, size)
+# per class, the heavy updates added to the sample, the attempt cap per
+# (class, size), and the smallest size a slot may fall to
 SAMPLING = {
-    "batched": {"rules": {"dense_ge3": (5000, 20_000_000), "sparse": (5000, 40_000_000)},
-                "heavy": 8, "max_attempts": 240},
-    "large": {"rules": {"dense": (20000, 20_000_000), "sparse": (20000, 40_000_000)},
-              "heavy": 8, "max_attempts": 120},
+    "batched": {"rules": {"dense_ge3": (1000, 5_000_000), "sparse": (1000, 5_000_000)},
+                "heavy": 8, "max_attempts": 60},
+    "served": {"rules": {"dense": (100, 2_400_000)}, "heavy": 8, "max_attempts": 80, "min_q": 5},
+    "large": {"rules": {"dense": (20000, 3_000_000), "sparse": (20000, 3_000_000)},
+              "heavy": 8, "max_attempts": 40, "min_q": 5},
 }
 DEFAULT_SAMPLING = {"rules": RULES, "heavy": 0, "max_attempts": 20000}
 
@@ -119,6 +120,8 @@ def main():
     if samp["max_attempts"] < DEFAULT_SAMPLING["max_attempts"]:
         rule += ("; at most %d attempts per (class, size), the slots left empty fall to the next smaller "
                  "size of the class" % samp["max_attempts"])
+        if "min_q" in samp:
+            rule += " (down to %d vertices)" % samp["min_q"]
     out = {"workload": wl, "graph_digest": w.graph.digest(), "batch": {"n_ins": ni, "n_del": nd, "sub": 0},
            "rule": rule, "queries": [], "rejected": []}
     want = {}
@@ -126,7 +129,7 @@ def main():
         want[(kind, q)] = want.get((kind, q), 0) + 1
     kinds = sorted({k for k, _ in want})
     qmax = {k: max(q for kk, q in want if kk == k) for k in kinds}
-    qmin = {k: min(q for kk, q in want if kk == k) for k in kinds}
+    qmin = {k: min([q for kk, q in want if kk == k] + [samp.get("min_q", 99)]) for k in kinds}
     # every size from the largest down to the smallest, so shortfalls can fall
     classes = [(k, q) for k in kinds for q in range(qmax[k], qmin[k] - 1, -1)]
     chosen = {c: [] for c in classes}
