@@ -434,7 +434,7 @@ def main():
     ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
                     help="plain: the metric's workload; batched / served: the A7 comparisons")
     ap.add_argument("--full-grid", action="store_true", help="batched mode: sweep the whole autotuner grid")
-    ap.add_argument("--batches", type=int, default=30, help="served mode: batches in the stream")
+    ap.add_argument("--batches", type=int, default=12, help="served mode: batches in the stream")
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 0.95],
                     help="served mode: offered load as fractions of the closed-loop capacity")
     args = ap.parse_args()

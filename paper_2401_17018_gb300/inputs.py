@@ -381,7 +381,7 @@ WORKLOADS = {
     "tiny": (11, 10_000, 4, None, 1),
     "mid": (20, 8_388_608, 8, 1.2, 1),
     "large": (23, 67_108_864, 16, 1.0, 1),
-    "served": (22, 33_554_432, 8, 1.2, 1),
+    "served": (22, 33_554_432, 8, None, 1),
 }
 
 

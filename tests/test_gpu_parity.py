@@ -455,3 +455,24 @@ def test_autotune_picks_a_point_and_keeps_counts(G):
         p2, n2 = G.gamma_recount_noalloc(ctx.h, len(qids))
         assert np.array_equal(p2, pos) and np.array_equal(n2, neg)
         ctx.commit()
+
+
+def test_instrumented_build_counts_bytes_only(G):
+    """GAMMA_F_COUNT_BYTES runs the DFS build that accounts algorithmic bytes:
+    same counts and per-update charges as the timed build, and it is the only
+    one that reports bytes."""
+    w = I.make_workload("tiny")
+    b = I.workload_batch(w, 400, 100, sub=5)
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)])]
+    res = {}
+    for flags in (G.GAMMA_F_PER_UPDATE, G.GAMMA_F_PER_UPDATE | G.GAMMA_F_COUNT_BYTES):
+        with G.Context(flags=flags) as ctx:
+            ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+            qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+            pos, neg = ctx.apply_batch(b.op, b.src, b.dst, qids)
+            per = [ctx.update_counts(j).tolist() for j in range(len(qids))]
+            res[flags] = (pos.tolist(), neg.tolist(), per, ctx.stats()["alg_bytes"])
+            ctx.commit()
+    plain, counted = res[G.GAMMA_F_PER_UPDATE], res[G.GAMMA_F_PER_UPDATE | G.GAMMA_F_COUNT_BYTES]
+    assert plain[:3] == counted[:3]
+    assert plain[3] == 0 and counted[3] > 0
