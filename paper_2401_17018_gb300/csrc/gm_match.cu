@@ -748,7 +748,10 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       const uint16_t chk_neq = P.samelab[c];
       if (ok && (chk_edge | chk_neq)) {
         uint32_t ee = e;
-        for (int l2 = lev; l2 >= 0 && ok; l2--) {
+        // walk the stored positions only down to the lowest one with a check
+        const uint32_t need_hi = (uint32_t)(chk_edge | chk_neq) & ~3u;
+        const int stop = need_hi ? __ffs(need_hi) - 3 : lev + 1;
+        for (int l2 = lev; l2 >= stop && ok; l2--) {
           const int pos = l2 + 2;
           const uint32_t vv = V[l2 * T + ee];
           if ((chk_neq >> pos) & 1) ok = (vv != id);
