@@ -179,6 +179,30 @@ GAMMA_API int gamma_commit(gamma_ctx *ctx);
  * returns GAMMA_EOVERFLOW when the entries do not fit (off is still filled). */
 GAMMA_API int gamma_export_adjacency(gamma_ctx *ctx, int64_t *off, int32_t *nbr, int32_t *tag, int64_t cap);
 
+/* Vertex updates (Sec. II-A treats a vertex insertion or deletion as edge
+ * updates; this build follows that reduction).  The vertex id and the label
+ * share one 32-bit adjacency key, so room for vertices added later must be
+ * reserved before gamma_load_graph: n_max is the largest vertex count the
+ * context will hold (0 = just the loaded n).  Affects the next load only;
+ * GAMMA_EINVAL for a negative n_max.  A graph loaded with a larger reserve
+ * must still satisfy 1 + ceil(log2 n_max) + label bits <= 32. */
+GAMMA_API int gamma_reserve_vertices(gamma_ctx *ctx, int32_t n_max);
+
+/* Append k isolated vertices with labels[k] (host or device; each in the
+ * loaded graph's label range [0, max label]).  They get ids n .. n+k-1
+ * (*out_first = n, may be NULL) and join G with no edges; edges to them are
+ * then inserted by ordinary batches.  GAMMA_ESTATE without a graph or with a
+ * staged batch; GAMMA_EINVAL for a bad label or when n + k exceeds the
+ * reserved id space (nothing changes then).  Registered queries stay. */
+GAMMA_API int gamma_add_vertices(gamma_ctx *ctx, int32_t k, const int32_t *labels, int32_t *out_first);
+
+/* The current neighbours of vertex v (host array out[cap], in the library's
+ * order: neighbour label, then id); *count = the degree.  Deleting a vertex
+ * is the batch that deletes these edges (the vertex stays, isolated).
+ * GAMMA_ESTATE with a staged batch; GAMMA_EOVERFLOW when cap < degree (the
+ * first cap ids are written). */
+GAMMA_API int gamma_vertex_neighbors(gamma_ctx *ctx, int32_t v, int32_t *out, int64_t cap, int64_t *count);
+
 /* Timings and sizes of the last apply/commit. */
 GAMMA_API int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out);
 

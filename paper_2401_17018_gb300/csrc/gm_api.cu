@@ -65,6 +65,8 @@ struct gamma_ctx {
   // graph
   bool loaded = false;
   int32_t n = 0;
+  int32_t n_reserve = 0;  // vertex count to make room for at the next load
+  int32_t n_cap = 0;      // vertices the loaded graph may grow to
   int idb = 1, nlab = 1, nlfw = 4;
   int32_t *d_label = nullptr;
   uint2 *d_adj = nullptr;
@@ -171,7 +173,30 @@ struct gamma_ctx {
 
 namespace {
 
+// a captured apply bakes the graph's device pointers into its kernels: forget
+// it whenever those arrays are freed or moved
+void drop_graph_exec(gamma_ctx *ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  ctx->gexec = nullptr;
+  ctx->gkey.clear();
+}
+
+// grow a per-vertex device array from n to n2 elements: old contents kept,
+// the new tail set to the byte `fill`
+template <typename T>
+int grow_vertex_array(gamma_ctx *ctx, T **arr, size_t per, int32_t n, int32_t n2, int fill) {
+  T *fresh = nullptr;
+  CKC(cudaMalloc((void **)&fresh, per * (size_t)n2));
+  CKC(cudaMemcpyAsync(fresh, *arr, per * (size_t)n, cudaMemcpyDeviceToDevice, ctx->stream));
+  CKC(cudaMemsetAsync(reinterpret_cast<char *>(fresh) + per * (size_t)n, fill, per * (size_t)(n2 - n), ctx->stream));
+  CKC(cudaStreamSynchronize(ctx->stream));
+  cudaFree(*arr);
+  *arr = fresh;
+  return GAMMA_OK;
+}
+
 void free_graph(gamma_ctx *ctx) {
+  drop_graph_exec(ctx);
   cudaFree(ctx->d_label); cudaFree(ctx->d_adj); cudaFree(ctx->d_cap);
   cudaFree(ctx->d_col); cudaFree(ctx->d_etag); cudaFree(ctx->d_nlf);
   cudaFree(ctx->d_hub_id); cudaFree(ctx->d_hub_lofs); cudaFree(ctx->d_hub_tab); cudaFree(ctx->d_hub_keys);
@@ -859,7 +884,8 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
   }
   ctx->n = n;
   ctx->nlab = (int)ctx->h_st->max_label + 1;
-  ctx->idb = bits_for(n);
+  ctx->n_cap = std::max(n, ctx->n_reserve);
+  ctx->idb = bits_for(ctx->n_cap);
   int lb = bits_for(ctx->nlab);
   if (1 + ctx->idb + lb > 32) {
     cudaFree(ts); cudaFree(td);
@@ -1117,6 +1143,71 @@ int gamma_export_adjacency(gamma_ctx *ctx, int64_t *off, int32_t *nbr, int32_t *
     off[v + 1] = k;
   }
   return k > cap ? ctx->fail(GAMMA_EOVERFLOW, "gamma_export_adjacency: %lld entries > cap", (long long)k) : GAMMA_OK;
+}
+
+int gamma_reserve_vertices(gamma_ctx *ctx, int32_t n_max) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (n_max < 0) return ctx->fail(GAMMA_EINVAL, "gamma_reserve_vertices: negative size");
+  ctx->n_reserve = n_max;
+  return GAMMA_OK;
+}
+
+int gamma_add_vertices(gamma_ctx *ctx, int32_t k, const int32_t *labels, int32_t *out_first) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "gamma_add_vertices: no graph loaded");
+  if (ctx->staged) return ctx->fail(GAMMA_ESTATE, "gamma_add_vertices: a batch is staged; commit it first");
+  if (k < 0 || (k > 0 && !labels)) return ctx->fail(GAMMA_EINVAL, "gamma_add_vertices: bad size or null labels");
+  if (out_first) *out_first = ctx->n;
+  if (k == 0) return GAMMA_OK;
+  const int64_t n2 = (int64_t)ctx->n + k;
+  if (n2 > ctx->n_cap)
+    return ctx->fail(GAMMA_EINVAL, "gamma_add_vertices: %lld vertices exceed the %d reserved "
+                     "(call gamma_reserve_vertices before gamma_load_graph)", (long long)n2, ctx->n_cap);
+  cudaSetDevice(ctx->device);
+  std::vector<int32_t> hl(k);
+  CKC(cudaMemcpy(hl.data(), labels, sizeof(int32_t) * k, cudaMemcpyDefault));
+  for (int32_t i = 0; i < k; i++)
+    if (hl[i] < 0 || hl[i] >= ctx->nlab)
+      return ctx->fail(GAMMA_EINVAL, "gamma_add_vertices: label %d of new vertex %d is outside the graph's "
+                       "labels [0, %d)", hl[i], i, ctx->nlab);
+  const int32_t n = ctx->n, m2 = (int32_t)n2;
+  drop_graph_exec(ctx);
+  CKC(cudaStreamSynchronize(ctx->stream));
+  // new vertices: no entries and no slot (their first insertion moves them to
+  // the pool), zero label counts, not hubs, in no staged group
+  CK(grow_vertex_array(ctx, &ctx->d_label, sizeof(int32_t), n, m2, 0));
+  CKC(cudaMemcpy(ctx->d_label + n, hl.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice));
+  CK(grow_vertex_array(ctx, &ctx->d_adj, sizeof(uint2), n, m2, 0));
+  CK(grow_vertex_array(ctx, &ctx->d_cap, sizeof(uint32_t), n, m2, 0));
+  CK(grow_vertex_array(ctx, &ctx->d_nlf, (size_t)ctx->nlfw, n, m2, 0));
+  CK(grow_vertex_array(ctx, &ctx->d_vgroup, sizeof(int32_t), n, m2, 0xff));
+  CK(grow_vertex_array(ctx, &ctx->d_hub_id, sizeof(int32_t), n, m2, 0xff));
+  for (int32_t i = 0; i < k; i++) ctx->label_freq[hl[i]]++;
+  ctx->n = m2;
+  return GAMMA_OK;
+}
+
+int gamma_vertex_neighbors(gamma_ctx *ctx, int32_t v, int32_t *out, int64_t cap, int64_t *count) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "gamma_vertex_neighbors: no graph loaded");
+  if (ctx->staged) return ctx->fail(GAMMA_ESTATE, "gamma_vertex_neighbors: a batch is staged; commit it first");
+  if (v < 0 || v >= ctx->n || !count || (cap > 0 && !out))
+    return ctx->fail(GAMMA_EINVAL, "gamma_vertex_neighbors: vertex out of range or null output");
+  cudaSetDevice(ctx->device);
+  CKC(cudaStreamSynchronize(ctx->stream));
+  uint2 a;
+  CKC(cudaMemcpy(&a, ctx->d_adj + v, sizeof(uint2), cudaMemcpyDeviceToHost));
+  *count = a.y;
+  if (a.y == 0) return GAMMA_OK;
+  std::vector<uint32_t> keys(a.y);
+  CKC(cudaMemcpy(keys.data(), ctx->d_col + a.x, sizeof(uint32_t) * a.y, cudaMemcpyDeviceToHost));
+  const uint32_t idmask = ctx->gd().idmask;
+  for (int64_t i = 0; i < (int64_t)a.y && i < cap; i++) out[i] = (int32_t)((keys[i] >> 1) & idmask);
+  return (int64_t)a.y > cap ? ctx->fail(GAMMA_EOVERFLOW, "gamma_vertex_neighbors: %u neighbours > cap", a.y)
+                            : GAMMA_OK;
 }
 
 int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out) {

@@ -86,6 +86,10 @@ _SIGS = {
     "gamma_commit": (ctypes.c_int, [_P]),
     "gamma_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(gamma_stats)]),
     "gamma_export_adjacency": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
+    "gamma_reserve_vertices": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "gamma_add_vertices": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32)]),
+    "gamma_vertex_neighbors": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64,
+                                              ctypes.POINTER(ctypes.c_int64)]),
     "gamma_set_options": (ctypes.c_int, [_P, ctypes.POINTER(gamma_options)]),
     "gamma_last_error": (ctypes.c_char_p, [_P]),
     "gamma_recount_noalloc": (ctypes.c_int, [_P, _P, _P]),
@@ -241,6 +245,32 @@ def gamma_export_adjacency(ctx: int, n: int, cap: int):
     return off, nbr[:off[-1]], tag[:off[-1]]
 
 
+def gamma_reserve_vertices(ctx: int, n_max: int) -> None:
+    _check(ctx, load_library().gamma_reserve_vertices(ctx, int(n_max)))
+
+
+def gamma_add_vertices(ctx: int, labels) -> int:
+    """Append len(labels) isolated vertices; returns the first new id."""
+    lab = _as(labels, np.int32)
+    first = ctypes.c_int32(0)
+    _check(ctx, load_library().gamma_add_vertices(ctx, int(len(lab)), _ptr(lab), ctypes.byref(first)))
+    return first.value
+
+
+def gamma_vertex_neighbors(ctx: int, v: int, cap: int = 1024) -> np.ndarray:
+    """Ids of v's current neighbours."""
+    lib = load_library()
+    while True:
+        out = np.zeros(max(cap, 1), np.int32)
+        cnt = ctypes.c_int64(0)
+        rc = lib.gamma_vertex_neighbors(ctx, int(v), _ptr(out), int(cap), ctypes.byref(cnt))
+        if rc == GAMMA_EOVERFLOW:
+            cap = int(cnt.value)
+            continue
+        _check(ctx, rc)
+        return out[:cnt.value]
+
+
 def gamma_set_options(ctx: int, options: gamma_options) -> None:
     _check(ctx, load_library().gamma_set_options(ctx, ctypes.byref(options)))
 
@@ -343,6 +373,15 @@ class Context:
     def export_adjacency(self, n: int):
         st = self.stats()
         return gamma_export_adjacency(self.h, n, int(st["pool_used"]))
+
+    def reserve_vertices(self, n_max: int):
+        gamma_reserve_vertices(self.h, n_max)
+
+    def add_vertices(self, labels) -> int:
+        return gamma_add_vertices(self.h, labels)
+
+    def vertex_neighbors(self, v: int) -> np.ndarray:
+        return gamma_vertex_neighbors(self.h, v)
 
 
 def gamma_autotune(ctx: int, grid, repeats: int = 1):

@@ -476,3 +476,88 @@ def test_instrumented_build_counts_bytes_only(G):
     plain, counted = res[G.GAMMA_F_PER_UPDATE], res[G.GAMMA_F_PER_UPDATE | G.GAMMA_F_COUNT_BYTES]
     assert plain[:3] == counted[:3]
     assert plain[3] == 0 and counted[3] > 0
+
+
+def _new_vertex_edges(n_old, k, seed):
+    """Edges from each of k new vertices (ids n_old..n_old+k-1) to three old
+    vertices, plus a path through the new ones; canonical and distinct."""
+    e = set()
+    r = I.rand_u64(seed, 72, np.arange(4 * k, dtype=np.uint64))
+    for i in range(k):
+        v = n_old + i
+        for j in range(3):
+            e.add((int(r[4 * i + j] % np.uint64(n_old)), v))
+        if i:
+            e.add((v - 1, v))
+    e = sorted(e)
+    return np.array([a for a, _ in e], np.int32), np.array([b for _, b in e], np.int32)
+
+
+def test_vertex_insertions_and_deletions(G):
+    """Vertex updates as edge batches (Sec. II-A): vertices added to a loaded
+    graph (id space reserved before loading) join with no edges; a batch then
+    inserts edges to them (mixed with ordinary updates), and deleting a vertex
+    is the batch of its incident edges. Counts and per-update charges equal the
+    oracle's on the grown graph, also with the apply replayed as a CUDA graph
+    whose captured pointers the new vertices invalidate."""
+    w = I.make_workload("tiny")
+    g = w.graph
+    k = 40
+    new_labels = (I.rand_u32(3, 71, np.arange(k, dtype=np.uint64)) % np.uint64(4)).astype(np.int32)
+    n2 = g.n + k
+    labels2 = np.concatenate([g.labels, new_labels])
+    ns, nd = _new_vertex_edges(g.n, k, 5)
+    base = I.workload_batch(w, 200, 60, sub=4)
+    op = np.concatenate([base.op, np.ones(ns.size, np.int8)])
+    src = np.concatenate([base.src, ns])
+    dst = np.concatenate([base.dst, nd])
+    mix = I.shuffle_order(op.size, 9, 3)
+    b1 = I.Batch(op[mix], src[mix], dst[mix])
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)]),
+          I.pattern_query([0, 0, 1, 1], [(0, 1), (1, 2), (2, 3), (3, 0)])]
+    for flags in (G.GAMMA_F_PER_UPDATE, G.GAMMA_F_PER_UPDATE | G.GAMMA_F_GRAPH):
+        with G.Context(flags=flags) as ctx:
+            ctx.reserve_vertices(n2)
+            ctx.load_graph(g.n, g.labels, g.src, g.dst)
+            qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+            # a batch of b1's size before the vertices arrive: in graph mode its
+            # captured apply would be replayed for b1 unless adding vertices drops it
+            pre = I.workload_batch(w, len(b1) - 10, 10, sub=8, pool_start=500)
+            ctx.apply_batch(pre.op, pre.src, pre.dst, qids)
+            ctx.commit()
+            cur = I.apply_batch_edges(g.src, g.dst, pre)
+            with pytest.raises(G.GammaError):
+                ctx.add_vertices(np.full(k, 99, np.int32))  # label outside the graph's range
+            assert ctx.add_vertices(new_labels) == g.n
+            with pytest.raises(G.GammaError):
+                ctx.add_vertices(np.zeros(1, np.int32))  # beyond the reserved vertex count
+            pos, neg = ctx.apply_batch(b1.op, b1.src, b1.dst, qids)
+            with pytest.raises(G.GammaError):
+                ctx.add_vertices(np.ones(1, np.int32))  # a batch is staged
+            per = np.stack([ctx.update_counts(j) for j in range(len(qids))])
+            ctx.commit()
+            want = O.bdsm_multi(n2, labels2, cur[0], cur[1], qs, b1)
+            assert np.array_equal(per, want)
+            assert pos.tolist() == want[:, b1.op > 0].sum(axis=1).tolist()
+            assert neg.tolist() == want[:, b1.op < 0].sum(axis=1).tolist()
+            cur = I.apply_batch_edges(cur[0], cur[1], b1)
+            # delete a new vertex and an old one: the batch of their incident edges
+            gone = [g.n + 7, int(ns[0])]
+            e = set()
+            for v in gone:
+                for u in ctx.vertex_neighbors(v).tolist():
+                    e.add((min(u, v), max(u, v)))
+            e = sorted(e)
+            assert len(e) >= 4
+            b2 = I.Batch(-np.ones(len(e), np.int8), np.array([a for a, _ in e], np.int32),
+                         np.array([c for _, c in e], np.int32))
+            pos2, neg2 = ctx.apply_batch(b2.op, b2.src, b2.dst, qids)
+            per2 = np.stack([ctx.update_counts(j) for j in range(len(qids))])
+            ctx.commit()
+            want2 = O.bdsm_multi(n2, labels2, cur[0], cur[1], qs, b2)
+            assert np.array_equal(per2, want2) and int(pos2.sum()) == 0
+            assert neg2.tolist() == want2.sum(axis=1).tolist()
+            for v in gone:
+                assert ctx.vertex_neighbors(v).size == 0
+            cur = I.apply_batch_edges(cur[0], cur[1], b2)
+            assert ctx.stats()["live_edges"] == 2 * cur[0].size
