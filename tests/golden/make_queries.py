@@ -59,7 +59,7 @@ RULES = {"dense": (200, 10_000_000), "dense_ge3": (200, 10_000_000), "sparse": (
 SAMPLING = {
     "batched": {"rules": {"dense_ge3": (1000, 20_000_000), "sparse": (1000, 20_000_000)},
                 "heavy": 8, "max_attempts": 60},
-    "served": {"rules": {"dense": (100, 2_400_000)}, "heavy": 8, "max_attempts": 80, "min_q": 5},
+    "served": {"rules": {"dense": (100, 2_400_000)}, "heavy": 8, "max_attempts": 200, "min_q": 5},
     "large": {"rules": {"dense": (20000, 3_000_000), "sparse": (20000, 3_000_000)},
               "heavy": 8, "max_attempts": 40, "min_q": 5},
 }
