@@ -414,9 +414,11 @@ def run_served(args):
         runs["%.2f" % load] = dict(per_form, identical_counts=same)
     line = {"metric": "served form: p50/p99 batch latency from arrival and sustained updates/s (1 GB300)",
             "mode": "served",
-            "config": {"workload": "served: R-MAT scale 22, %d queries of 6..8 vertices, %d batches of "
-                                   "floor(10^U(3,6)) updates (ins:del 1:1), Poisson arrivals" % (
-                                       len(queries), len(stream_b)), "updates": total},
+            "config": {"workload": "served: R-MAT scale 22, 8 uniform labels, %d dense queries of %d..%d "
+                                   "vertices, %d batches of floor(10^U(3,6)) updates (ins:del 1:1), Poisson "
+                                   "arrivals" % (len(queries), min(q.labels.size for q in queries),
+                                                 max(q.labels.size for q in queries), len(stream_b)),
+                       "updates": total},
             "closed_loop_capacity_updates_per_s": cap, "loads": runs}
     print(json.dumps(line), flush=True)
     ctx.close()
