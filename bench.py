@@ -351,7 +351,7 @@ def run_served(args):
     if qd.get("graph_digest") not in (None, w.graph.digest()):
         raise SystemExit("stored queries were chosen on a different graph")
     queries = [I.Query.from_json(x) for x in qd["queries"]]
-    stream_b = I.served_stream(w, args.batches, w.seed)
+    stream_b = I.served_stream(w, args.batches, w.seed, args.size_exp[0], args.size_exp[1])
     total = sum(len(b) for b in stream_b)
     g = w.graph
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -415,9 +415,10 @@ def run_served(args):
     line = {"metric": "served form: p50/p99 batch latency from arrival and sustained updates/s (1 GB300)",
             "mode": "served",
             "config": {"workload": "served: R-MAT scale 22, 8 uniform labels, %d dense queries of %d..%d "
-                                   "vertices, %d batches of floor(10^U(3,6)) updates (ins:del 1:1), Poisson "
+                                   "vertices, %d batches of floor(10^U(%g,%g)) updates (ins:del 1:1), Poisson "
                                    "arrivals" % (len(queries), min(q.labels.size for q in queries),
-                                                 max(q.labels.size for q in queries), len(stream_b)),
+                                                 max(q.labels.size for q in queries), len(stream_b),
+                                                 args.size_exp[0], args.size_exp[1]),
                        "updates": total},
             "closed_loop_capacity_updates_per_s": cap, "loads": runs}
     print(json.dumps(line), flush=True)
@@ -437,6 +438,8 @@ def main():
                     help="plain: the metric's workload; batched / served: the A7 comparisons")
     ap.add_argument("--full-grid", action="store_true", help="batched mode: sweep the whole autotuner grid")
     ap.add_argument("--batches", type=int, default=12, help="served mode: batches in the stream")
+    ap.add_argument("--size-exp", type=float, nargs=2, default=[3.0, 6.0],
+                    help="served mode: batch sizes floor(10^U(a, b))")
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 0.95],
                     help="served mode: offered load as fractions of the closed-loop capacity")
     args = ap.parse_args()
