@@ -2,8 +2,8 @@
 """Benchmark of batch-dynamic subgraph matching (BDSM) on GB300.
 
 One step = one pass of the whole hot path over one update batch: stage the
-batch into the device-resident dynamic CSR (A1), seed (A2), DFS extension
-(A5) with match counting (A6), counts back to the host, commit (A8).
+batch into the device-resident dynamic CSR, seed, DFS extension with match
+counting, counts back to the host, commit.
 Steps alternate the batch and its inverse, so the graph cycles between G0
 and G0 + batch and every step does the same amount of work.
 
@@ -17,8 +17,9 @@ available). The graph (about 60 MB of adjacency) fits in L2, so L2 is flushed
 
 value   = updates/s with the batch already in HBM (device events per step)
 e2e     = the same metric through the C-ABI with host (pinned) batch buffers
-roofline: the DFS kernel's algorithmic bytes (SURVEY-d accounting, counted by
-          an instrumented launch) / its measured duration, against the
+roofline: the DFS kernel's algorithmic bytes (per candidate slot, search
+          step, probe and prepared entry; counted by an untimed launch of the
+          instrumented build) / the timed launch's duration, against the
           measured HBM copy bandwidth
 cpu_baseline: the CPU oracle on a bounded sample of the same batch.
 --impl reference times that oracle alone, as the reference arm.
@@ -251,7 +252,7 @@ def config_of(workload, b, nq):
 
 
 def run_batched(args):
-    """Batched form (A7): the same batch and the 64 stored batched queries,
+    """Batched form: the same batch and the 64 stored batched queries,
     (1) plain: one seed + DFS launch sequence per query, (2) batched: one
     launch over all queries' seeds, autotuned and replayed as a CUDA graph.
     Both must give identical counts."""
@@ -337,7 +338,7 @@ def run_batched(args):
 
 
 def run_served(args):
-    """Served form (A7): a stream of uneven batches arriving as a Poisson
+    """Served form: a stream of uneven batches arriving as a Poisson
     process at a fraction of the closed-loop capacity; one request at a time
     ("plain") vs continuous batching ("served"); latency from arrival."""
     import threading as th
@@ -435,7 +436,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-query", action="store_true", help="plain form: one launch sequence per query")
     ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
-                    help="plain: the metric's workload; batched / served: the A7 comparisons")
+                    help="plain: the metric's workload; batched / served: the batched and served forms")
     ap.add_argument("--full-grid", action="store_true", help="batched mode: sweep the whole autotuner grid")
     ap.add_argument("--batches", type=int, default=12, help="served mode: batches in the stream")
     ap.add_argument("--size-exp", type=float, nargs=2, default=[3.0, 6.0],

@@ -84,11 +84,11 @@ typedef struct {
 } gamma_matches;
 
 typedef struct {
-  double ms_stage;     /* A1: batch validation + staging into the dynamic CSR */
-  double ms_seed;      /* A2: seeding */
-  double ms_match;     /* A5: DFS extension */
-  double ms_finalize;  /* A6: count reduction and row compaction */
-  double ms_commit;    /* A8: last commit */
+  double ms_stage;     /* batch validation + staging into the dynamic CSR */
+  double ms_seed;      /* seeding */
+  double ms_match;     /* DFS extension */
+  double ms_finalize;  /* count reduction and row compaction */
+  double ms_commit;    /* last commit */
   int64_t seeds;       /* seeds that passed the label and filter tests */
   int64_t work_items;  /* DFS work items (seeds split by steal_grain) */
   int64_t touched;     /* vertices whose adjacency the last batch touched */
@@ -166,12 +166,12 @@ GAMMA_API int gamma_fetch_matches(gamma_ctx *ctx, gamma_matches *out);
  * incremental matches charged to update k.  Needs GAMMA_F_PER_UPDATE. */
 GAMMA_API int gamma_update_counts(gamma_ctx *ctx, int32_t j, uint64_t *out);
 
-/* Make G' the current graph: drop deleted edges, clear batch tags (A8).
+/* Make G' the current graph: drop deleted edges, clear batch tags.
  * GAMMA_ESTATE if no batch is staged. */
 GAMMA_API int gamma_commit(gamma_ctx *ctx);
 
 /* Copy the current adjacency to host arrays, for checking the dynamic CSR
- * (A1/A8) against a host model.  While a batch is staged this is the union
+ * (staging and commit) against a host model.  While a batch is staged this is the union
  * graph G u G'.  off[n+1] (int64) delimits each vertex's list; for entry i,
  * nbr[i] is the neighbour id and tag[i] is -1 for an edge the staged batch
  * does not touch, else 2 * (update index) + (1 for a deletion).  Lists are in

@@ -1,7 +1,7 @@
 // gm_api.cu -- the C-ABI of libgamma (include/gamma.h): context and state
 // machine, host planner (matching orders, Alg. 1 input pi), buffer management
-// and the launch sequence of one batch: stage (A1) -> seed (A2) -> DFS (A5)
-// with row compaction (A6) -> counts to the host; commit (A8) separately.
+// and the launch sequence of one batch: stage -> seed -> DFS with row
+// compaction -> counts to the host; commit separately.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -414,7 +414,7 @@ int prepare_buffers(gamma_ctx *ctx, int64_t b) {
   return build_tables(ctx, ctx->qids, (ctx->flags & GAMMA_F_PER_QUERY) != 0);
 }
 
-// status reset + stage (A1); no host sync
+// status reset + stage; no host sync
 int enqueue_stage(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const int32_t *ddst) {
   cudaStream_t s = ctx->stream;
   CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st_init, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
@@ -424,7 +424,7 @@ int enqueue_stage(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const 
   return GAMMA_OK;
 }
 
-// seed (A2) + DFS (A5, A6) for the staged batch, then counts and status to
+// seed + DFS (with counting and rows) for the staged batch, then counts and status to
 // the host; no host sync.  The kernels do nothing once an error is flagged.
 int enqueue_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_stride, bool clear_err) {
   const int nq = (int)ctx->qids.size();

@@ -1,6 +1,6 @@
 // gm_graph.cu -- the device-resident dynamic CSR: bulk load, batch staging
-// (A1: validate the batch, merge insertions into the sorted lists, tag
-// deletions), commit (A8: drop deleted entries, clear tags) and the per-label
+// (validate the batch, merge insertions into the sorted lists, tag
+// deletions), commit (drop deleted entries, clear tags) and the per-label
 // neighbour counts of the union graph G u G' used by the candidate filter
 // (the neighbourhood-label-frequency test of Sec. IV-B, as counts).
 //

@@ -1,4 +1,4 @@
-"""The device-resident dynamic CSR (A1 staging, A8 commit) against a host
+"""The device-resident dynamic CSR (staging and commit) against a host
 set model: after staging, every list is the union G u G' sorted by (label,
 id) with update tags on the batch's edges; after commit, it is G'."""
 import numpy as np
