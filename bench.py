@@ -557,7 +557,9 @@ def main():
                 "d2h_bytes_per_step": 16 * len(queries) + 3 * STATUS_BYTES},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": "k_dfs", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": dfs_traffic(), "peak_kind": peak_kind,
+                     "frac": achieved / peak,
+                     "traffic": dfs_traffic() if args.workload == "mid" else None,  # recorded on mid only
+                     "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": dfs_ms},
         "clocks": clk,
     }
