@@ -256,3 +256,44 @@ def test_planted_mistakes_are_caught():
     b3 = I.Batch(b.op[:2].copy(), b.src[:2].copy(), b.dst[:2].copy())
     c3, _ = O.bdsm(d["n"], lab, s, t, q, b3)
     assert O.totals(c3, b3.op) == (6, 0)
+
+
+@pytest.mark.parametrize("trial", range(6))
+def test_vertex_updates_as_edge_batches(trial):
+    """Sec. II-A treats vertex updates as edge updates. Pinned by brute force:
+    (1) deleting every edge of a vertex v makes exactly the embeddings of G
+    that use v vanish (a connected query with >= 2 vertices uses one of v's
+    edges whenever it uses v), and nothing appears; (2) inserting a new
+    vertex's edges makes exactly the embeddings of G' that use it appear;
+    (3) isolated extra vertices change no count."""
+    g = I.random_small_graph(14, 40, 2, 7, trial)
+    qs = [I.pattern_query([0, 1, 1], [(0, 1), (1, 2)]), I.TRIANGLE_WITH_TAIL if trial % 2 else
+          I.pattern_query([0, 0, 1], [(0, 1), (1, 2), (0, 2)])]
+    edges = {(min(int(a), int(b)), max(int(a), int(b))) for a, b in zip(g.src, g.dst)}
+    deg = np.bincount(np.concatenate([g.src, g.dst]), minlength=g.n)
+    v = int(np.argmax(deg))
+    inc = sorted(e for e in edges if v in e)
+    dele = I.Batch(-np.ones(len(inc), np.int8), np.array([a for a, _ in inc], np.int32),
+                   np.array([b for _, b in inc], np.int32))
+    # a new vertex n joined to the neighbours of v (and v), labelled like v
+    n2 = g.n + 1
+    lab2 = np.concatenate([g.labels, g.labels[v:v + 1]])
+    new = sorted({(min(u, g.n), max(u, g.n)) for e in inc for u in e} )
+    ins = I.Batch(np.ones(len(new), np.int8), np.array([a for a, _ in new], np.int32),
+                  np.array([b for _, b in new], np.int32))
+    for q in qs:
+        emb = O.brute_embeddings(g.n, g.labels, edges, q)
+        using_v = {m for m in emb if v in m}
+        c, t = O.bdsm(g.n, g.labels, g.src, g.dst, q, dele, want_tuples=True)
+        pos, neg = O.totals(c, dele.op)
+        assert pos == 0 and neg == len(using_v)
+        assert _tupset(t, -1) == using_v
+        # (3) isolated extra vertex: same counts as on the original graph
+        c3, _ = O.bdsm(n2, lab2, g.src, g.dst, q, dele)
+        assert np.array_equal(c3, c)
+        # (2) the new vertex's edges, on the graph with the vertex added
+        emb2 = O.brute_embeddings(n2, lab2, edges | set(new), q)
+        c2, t2 = O.bdsm(n2, lab2, g.src, g.dst, q, ins, want_tuples=True)
+        pos2, neg2 = O.totals(c2, ins.op)
+        assert neg2 == 0 and _tupset(t2, 1) == {m for m in emb2 if g.n in m}
+        assert pos2 == len({m for m in emb2 if g.n in m})
