@@ -12,8 +12,9 @@
  * charged to exactly one update, the lowest-indexed one among those edges
  * (Sec. IV-C: a total order over updates so that no match is found twice).
  *
- * State machine: create -> load_graph -> register_query* ->
- *   (apply_batch -> [fetch_matches | update_counts]* -> commit)* -> destroy.
+ * State machine: create -> [reserve_vertices] -> load_graph -> register_query* ->
+ *   (apply_batch -> [fetch_matches | update_counts]* -> commit | add_vertices)*
+ *   -> destroy.
  * A second apply_batch before commit returns GAMMA_ESTATE.
  *
  * Pointers: every input array may be host memory (pageable or pinned) or
