@@ -1,0 +1,55 @@
+"""The multi-rank path of bench.py on the CPU (gloo, world size 2).
+
+The path does not shard: every rank is an independent replica of the whole
+workload, so the only cross-rank step is the maximum of the timed seconds,
+from which rank 0 reports the whole job's rate.
+"""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local = 1.5 + rank  # rank 1 is the slow one
+        got = bench.max_over_ranks(local, dist, "cpu")
+        rate = bench.whole_job_rate(300, world, got)
+        out.put((rank, got, rate))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_ranks_agree_on_the_slowest_time_and_the_job_rate():
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [2.5, 2.5]
+    assert [r[2] for r in res] == [240.0, 240.0]  # 2 replicas x 300 units in 2.5 s
+
+
+def test_single_rank_needs_no_collective():
+    assert bench.max_over_ranks(3.0) == 3.0
+    assert bench.whole_job_rate(100, 1, 4.0) == 25.0
