@@ -561,3 +561,80 @@ def test_vertex_insertions_and_deletions(G):
                 assert ctx.vertex_neighbors(v).size == 0
             cur = I.apply_batch_edges(cur[0], cur[1], b2)
             assert ctx.stats()["live_edges"] == 2 * cur[0].size
+
+
+def _max_query_case():
+    """16-vertex queries (the limit): a star whose centre has one neighbour per
+    leaf label (two for labels 1..5 once the batch lands) and a path labelled
+    0..15 that one inserted edge completes."""
+    n = 64
+    lab = np.zeros(n, np.int32)
+    edges = set()
+    for i in range(1, 16):
+        lab[i] = i; edges.add((0, i))
+    for i in range(16, 21):
+        lab[i] = i - 15                       # second candidates for labels 1..5
+    for k in range(16):                       # path 21..36 labelled 0..15
+        lab[21 + k] = k
+        if k: edges.add((20 + k, 21 + k))
+    r = I.rand_u64(3, 91, np.arange(200, dtype=np.uint64))
+    for j in range(37, 64):
+        lab[j] = int(r[j] % np.uint64(16))
+    for t in range(60):
+        a, b = 37 + int(r[2 * t] % np.uint64(27)), 37 + int(r[2 * t + 1] % np.uint64(27))
+        if a != b: edges.add((min(a, b), max(a, b)))
+    edges.discard((28, 29))                   # the path is completed by the batch
+    src = np.array([a for a, _ in sorted(edges)], np.int32); dst = np.array([b for _, b in sorted(edges)], np.int32)
+    ins = [(0, 16), (0, 17), (0, 18), (28, 29), (37, 38) if (37, 38) not in edges else (39, 40)]
+    dels = [(0, 3), sorted(e for e in edges if e[0] >= 37)[0]]
+    op = np.array([1] * len(ins) + [-1] * len(dels), np.int8)
+    bs = np.array([a for a, _ in ins + dels], np.int32); bd = np.array([b for _, b in ins + dels], np.int32)
+    mix = I.shuffle_order(op.size, 4, 2)
+    b = I.Batch(op[mix], bs[mix], bd[mix])
+    star = I.pattern_query([0] + list(range(1, 16)), [(0, i) for i in range(1, 16)])
+    path = I.pattern_query(list(range(16)), [(i, i + 1) for i in range(15)])
+    return I.Graph(n, lab, src, dst), [star, path], b
+
+
+def _wide_key_case():
+    """The widest adjacency key: 2^23 vertices and labels up to 255 fill all 32
+    bits (23 id bits, 8 label bits, the batch flag); the matches sit on the
+    top ids and labels."""
+    n = 1 << 23                                # 23 id bits + 8 label bits + flag = 32
+    lab = np.zeros(n, np.int32)
+    r = I.rand_u64(5, 92, np.arange(4000, dtype=np.uint64))
+    hi = n - 1 - np.arange(40)                 # the top ids carry labels 254 / 255
+    lab[hi] = np.where(np.arange(40) % 2 == 0, 255, 254)
+    lab[7] = 128
+    edges = set()
+    for t in range(300):
+        a, b = int(hi[r[2 * t] % np.uint64(40)]), int(hi[r[2 * t + 1] % np.uint64(40)])
+        if a != b: edges.add((min(a, b), max(a, b)))
+    for t in range(40):                        # a spread of low ids joined to the top ones
+        a, b = int(r[1000 + t] % np.uint64(n - 64)), int(hi[t])
+        edges.add((min(a, b), max(a, b)))
+    edges.add((7, int(hi[0])))
+    e = sorted(edges)
+    keep, batch_e = e[:-30], e[-30:]
+    src = np.array([a for a, _ in keep], np.int32); dst = np.array([b for _, b in keep], np.int32)
+    dels = keep[:10]
+    op = np.array([1] * len(batch_e) + [-1] * len(dels), np.int8)
+    bs = np.array([a for a, _ in batch_e + dels], np.int32); bd = np.array([b for _, b in batch_e + dels], np.int32)
+    mix = I.shuffle_order(op.size, 6, 2)
+    b = I.Batch(op[mix], bs[mix], bd[mix])
+    qs = [I.pattern_query([255, 254, 255], [(0, 1), (1, 2), (0, 2)]),
+          I.pattern_query([128, 255, 254, 255], [(0, 1), (1, 2), (2, 3)]),
+          I.pattern_query([0, 255, 254], [(0, 1), (1, 2)])]
+    return I.Graph(n, lab, src, dst), qs, b
+
+
+def test_sixteen_vertex_queries(G):
+    g, qs, b = _max_query_case()
+    pos, neg, _ = check(G, g, qs, b)
+    assert (int(pos[0]), int(neg[0]), int(pos[1])) == (4, 1, 1)
+
+
+def test_widest_adjacency_key(G):
+    g, qs, b = _wide_key_case()
+    pos, neg, _ = check(G, g, qs, b)
+    assert int(pos.sum()) > 0 and int(neg.sum()) > 0
