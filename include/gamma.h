@@ -249,8 +249,11 @@ GAMMA_API int gamma_recount_noalloc(gamma_ctx *ctx, uint64_t *out_pos, uint64_t 
  * request still gets exactly its own result) and commits them.  A group
  * stops at the first request that touches an edge already in the group, at
  * max_requests / max_updates, or when its estimated device memory would
- * exceed hbm_fraction of the free HBM (admission).  While a server runs, its
- * context belongs to the worker thread: call nothing else on it.
+ * exceed hbm_fraction of the free HBM (admission).  A group that contains an
+ * invalid request is served again one request at a time, so only the invalid
+ * request fails (GAMMA_EINVAL) and the others get their one-at-a-time
+ * results.  While a server runs, its context belongs to the worker thread:
+ * call nothing else on it.
  * ------------------------------------------------------------------------ */
 typedef struct gamma_server gamma_server;
 

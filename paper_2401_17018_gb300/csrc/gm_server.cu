@@ -130,28 +130,49 @@ struct gamma_server {
 
   int ctx_device();
 
+  // stage requests [i0, i1) of the group together and commit them; returns
+  // the status, counts in pos/neg at the requests' positions
+  int apply_range(std::vector<Request *> &group, size_t i0, size_t i1, std::vector<uint64_t> &pos,
+                  std::vector<uint64_t> &neg) {
+    int64_t n = 0;
+    for (size_t i = i0; i < i1; i++) n += group[i]->b;
+    int rc = ensure_group(n);
+    if (rc != GAMMA_OK) return rc;
+    const int nq = (int)qids.size();
+    std::vector<int64_t> off(i1 - i0 + 1, 0);
+    for (size_t i = i0; i < i1; i++) {
+      Request *r = group[i];
+      const int64_t o = off[i - i0];
+      memcpy(g_op + o, r->op, r->b);
+      memcpy(g_src + o, r->src, 4 * r->b);
+      memcpy(g_dst + o, r->dst, 4 * r->b);
+      off[i - i0 + 1] = o + r->b;
+    }
+    rc = gamma_apply_batches(ctx, (int32_t)(i1 - i0), off.data(), g_op, g_src, g_dst, nq, qids.data(),
+                             pos.data() + i0 * nq, neg.data() + i0 * nq);
+    if (rc == GAMMA_OK || rc == GAMMA_ETIMEOUT) {
+      int rc2 = gamma_commit(ctx);
+      if (rc == GAMMA_OK) rc = rc2;
+    }
+    return rc;
+  }
+
   void run_group(std::vector<Request *> &group) {
     const double start = now_ms(t0);
     int64_t n = 0;
     for (Request *r : group) n += r->b;
-    int rc = ensure_group(n);
-    std::vector<int64_t> off(group.size() + 1, 0);
     const int nq = (int)qids.size();
     std::vector<uint64_t> pos(group.size() * std::max(nq, 1)), neg(pos.size());
-    if (rc == GAMMA_OK) {
-      for (size_t i = 0; i < group.size(); i++) {
-        Request *r = group[i];
-        memcpy(g_op + off[i], r->op, r->b);
-        memcpy(g_src + off[i], r->src, 4 * r->b);
-        memcpy(g_dst + off[i], r->dst, 4 * r->b);
-        off[i + 1] = off[i] + r->b;
-      }
-      rc = gamma_apply_batches(ctx, (int32_t)group.size(), off.data(), g_op, g_src, g_dst, nq, qids.data(),
-                               pos.data(), neg.data());
-      if (rc == GAMMA_OK || rc == GAMMA_ETIMEOUT) {
-        int rc2 = gamma_commit(ctx);
-        if (rc == GAMMA_OK) rc = rc2;
-      }
+    std::vector<int> status(group.size(), GAMMA_OK);
+    int rc = apply_range(group, 0, group.size(), pos, neg);
+    if (rc == GAMMA_EINVAL && group.size() > 1) {
+      // some request is invalid (the whole group was rejected, the graph is
+      // unchanged): serve the requests one by one, in order, so that only the
+      // invalid ones fail and every other request meets the graph left by
+      // the valid requests before it, as one-at-a-time serving would give
+      for (size_t i = 0; i < group.size(); i++) status[i] = apply_range(group, i, i + 1, pos, neg);
+    } else {
+      for (auto &x : status) x = rc;
     }
     const double done = now_ms(t0);
     std::lock_guard<std::mutex> lk(mu);
@@ -160,7 +181,7 @@ struct gamma_server {
       r->start_ms = start;
       r->done_ms = done;
       r->group = (int32_t)group.size();
-      r->status = rc;
+      r->status = status[i];
       r->pos.assign(pos.begin() + i * nq, pos.begin() + (i + 1) * nq);
       r->neg.assign(neg.begin() + i * nq, neg.begin() + (i + 1) * nq);
       r->done = true;

@@ -638,3 +638,50 @@ def test_widest_adjacency_key(G):
     g, qs, b = _wide_key_case()
     pos, neg, _ = check(G, g, qs, b)
     assert int(pos.sum()) > 0 and int(neg.sum()) > 0
+
+
+def test_server_isolates_an_invalid_request(G):
+    """A request that deletes a missing edge fails alone: the requests staged
+    with it get the results of serving the valid requests one at a time."""
+    w = I.make_workload("tiny")
+    reqs = _requests(w, [int(x) for x in np.random.default_rng(4).integers(1, 20, 24)], 13)
+    g = w.graph
+    have = set(I.edge_keys(g.src, g.dst).tolist())
+    a = 0
+    while True:  # a vertex pair that is never an edge during the stream
+        u, v = 3 + a, 1000 + a
+        touched = any(int(k) == (u << 32 | v) for r in reqs for k in I.edge_keys(r.src, r.dst))
+        if (u << 32 | v) not in have and not touched:
+            break
+        a += 1
+    bad_at = {5, 17}
+    stream = []
+    for i, r in enumerate(reqs):
+        if i in bad_at:
+            stream.append(I.Batch(np.array([-1], np.int8), np.array([u], np.int32), np.array([v], np.int32)))
+        stream.append(r)
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)])]
+    alone = []
+    with G.Context() as ctx:
+        ctx.load_graph(g.n, g.labels, g.src, g.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        for r in reqs:
+            pos, neg = ctx.apply_batch(r.op, r.src, r.dst, qids)
+            alone.append((pos.tolist(), neg.tolist()))
+            ctx.commit()
+    with G.Context() as ctx:
+        ctx.load_graph(g.n, g.labels, g.src, g.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        srv = G.Server(ctx, qids, max_requests=16)
+        tickets = [srv.submit(r.op, r.src, r.dst) for r in stream]
+        got, bad = [], 0
+        for t, r in zip(tickets, stream):
+            rc, pos, neg, info = srv.wait(t)
+            if len(r) == 1 and int(r.src[0]) == u and int(r.dst[0]) == v:
+                assert rc == G.GAMMA_EINVAL
+                bad += 1
+            else:
+                assert rc == G.GAMMA_OK
+                got.append((pos.tolist(), neg.tolist()))
+        srv.stop()
+    assert bad == len(bad_at) and got == alone
