@@ -284,6 +284,8 @@ def run_batched(args):
         raise SystemExit("stored queries were chosen on a different graph")
     queries = [I.Query.from_json(x) for x in qd["queries"]]
     batch = I.workload_batch(w, 90_000, 10_000)
+    if args.first:
+        batch = I.Batch(batch.op[:args.first].copy(), batch.src[:args.first].copy(), batch.dst[:args.first].copy())
     inv = batch.inverse()
     g = w.graph
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -342,9 +344,12 @@ def run_batched(args):
     same = counts["plain"] == counts["batched"]
     line = {"metric": "batched vs plain per-query launches: updates/s and p99 batch latency (1 GB300)",
             "mode": "batched", "config": {"workload": "batched: R-MAT scale 20, %d queries of %d..%d vertices "
-                                                      "(sparse and dense alternating), batch 100000 (90000 ins + "
-                                                      "10000 del)" % (len(queries), min(q.labels.size for q in queries),
-                                                                      max(q.labels.size for q in queries))},
+                                                      "(sparse and dense alternating), %s" % (
+                                                          len(queries), min(q.labels.size for q in queries),
+                                                          max(q.labels.size for q in queries),
+                                                          "the first %d updates of the batch" % len(batch)
+                                                          if args.first else "batch 100000 (90000 ins + 10000 del)"),
+                                          "batch_updates": len(batch)},
             "steps": args.steps, "warmup": args.warmup, "identical_counts": same,
             "incremental_matches_per_step": int(sum(counts["plain"][0]) + sum(counts["plain"][1])) if counts["plain"] else None,
             "plain": out["plain"], "batched": out["batched"],
@@ -455,6 +460,8 @@ def main():
     ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
                     help="plain: the metric's workload; batched / served: the batched and served forms")
     ap.add_argument("--full-grid", action="store_true", help="batched mode: sweep the whole autotuner grid")
+    ap.add_argument("--first", type=int, default=0,
+                    help="batched mode: keep only the first N updates of the batch (0 = all)")
     ap.add_argument("--batches", type=int, default=12, help="served mode: batches in the stream")
     ap.add_argument("--size-exp", type=float, nargs=2, default=[3.0, 6.0],
                     help="served mode: batch sizes floor(10^U(a, b))")
