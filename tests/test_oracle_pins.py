@@ -297,3 +297,53 @@ def test_vertex_updates_as_edge_batches(trial):
         pos2, neg2 = O.totals(c2, ins.op)
         assert neg2 == 0 and _tupset(t2, 1) == {m for m in emb2 if g.n in m}
         assert pos2 == len({m for m in emb2 if g.n in m})
+
+
+def _is_valid_row(row, q, labels, g_edges, g2_edges, batch):
+    """A row (charged update k, sign, phi) of the oracle, checked against the
+    definitions directly: phi is injective and label-preserving, every query
+    edge maps to an edge of the right view (G' for +, G for -), and k is the
+    smallest index among the same-sign updates whose edge is a query-edge image."""
+    k, sign = int(row[0]), int(row[1])
+    phi = [int(x) for x in row[2:]]
+    if len(set(phi)) != q.q or any(labels[phi[u]] != q.labels[u] for u in range(q.q)):
+        return False
+    view = g2_edges if sign > 0 else g_edges
+    images = {(min(phi[a], phi[b]), max(phi[a], phi[b])) for a, b in zip(q.src.tolist(), q.dst.tolist())}
+    if not images <= view:
+        return False
+    same = [i for i in range(len(batch)) if int(batch.op[i]) == sign and
+            (min(int(batch.src[i]), int(batch.dst[i])), max(int(batch.src[i]), int(batch.dst[i]))) in images]
+    return bool(same) and min(same) == k
+
+
+BULK_QUERIES = SMALL_QUERIES + [
+    I.pattern_query([0, 1, 0, 1, 0], [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0)]),           # 5-cycle
+    I.pattern_query([0, 0, 1, 1, 0], [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (1, 4)]),   # house
+]
+
+
+def test_incremental_equals_static_difference_bulk():
+    """2,000 more random cases (6..12 vertices, 2..3 labels, 1..6 mixed
+    updates, queries of 2..5 vertices): the oracle's counts and rows equal the
+    static difference, and each row is valid under the definitions."""
+    checked = 0
+    for trial in range(2000):
+        n = 6 + trial % 7
+        g = I.random_small_graph(n, 30 + (trial * 7) % 40, 2 + trial % 2, 11, trial)
+        b = _random_batch(g, 1000 + trial, 1 + trial % 4, trial % 3)
+        if len(b) == 0:
+            continue
+        ge = {(min(a, c), max(a, c)) for a, c in zip(g.src.tolist(), g.dst.tolist())}
+        s2, d2 = I.apply_batch_edges(g.src, g.dst, b)
+        g2e = {(min(a, c), max(a, c)) for a, c in zip(s2.tolist(), d2.tolist())}
+        for q in BULK_QUERIES:
+            pos, neg, _ = O.brute_bdsm(g.n, g.labels, g.src, g.dst, q, b)
+            c, tup = O.bdsm(g.n, g.labels, g.src, g.dst, q, b, want_tuples=True)
+            assert O.totals(c, b.op) == (len(pos), len(neg))
+            assert {(int(r[1]), tuple(int(x) for x in r[2:])) for r in tup} == \
+                {(1, p) for p in pos} | {(-1, p) for p in neg}
+            for r in tup:
+                assert _is_valid_row(r, q, g.labels, ge, g2e, b)
+            checked += len(tup)
+    assert checked > 5000
