@@ -204,6 +204,20 @@ GAMMA_API int gamma_add_vertices(gamma_ctx *ctx, int32_t k, const int32_t *label
  * first cap ids are written). */
 GAMMA_API int gamma_vertex_neighbors(gamma_ctx *ctx, int32_t v, int32_t *out, int64_t cap, int64_t *count);
 
+/* Checkpoint and restore (no counterpart in the paper; commit is the
+ * consistency point).  gamma_checkpoint writes the committed graph (labels,
+ * edges, reserved vertex count) and the registered queries into the host
+ * buffer buf[cap] and sets *size to the bytes needed; GAMMA_EOVERFLOW when
+ * cap is too small (nothing partial is usable then; call again with *size),
+ * GAMMA_ESTATE without a graph or with a staged batch.  gamma_restore
+ * replaces the context's graph and queries with a checkpoint through the
+ * ordinary load and register calls (same validation), so the queries keep
+ * their ids; GAMMA_EINVAL for a damaged checkpoint.  The format is a plain
+ * byte layout of int32 words (see the library source); it is not meant to
+ * move between machines of different endianness. */
+GAMMA_API int gamma_checkpoint(gamma_ctx *ctx, void *buf, int64_t cap, int64_t *size);
+GAMMA_API int gamma_restore(gamma_ctx *ctx, const void *buf, int64_t size);
+
 /* Timings and sizes of the last apply/commit. */
 GAMMA_API int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out);
 

@@ -1145,6 +1145,122 @@ int gamma_export_adjacency(gamma_ctx *ctx, int64_t *off, int32_t *nbr, int32_t *
   return k > cap ? ctx->fail(GAMMA_EOVERFLOW, "gamma_export_adjacency: %lld entries > cap", (long long)k) : GAMMA_OK;
 }
 
+// checkpoint layout (little-endian int32 words unless noted):
+//   "GMCK" (4 bytes), version 1, n, n_cap, m (int64), labels[n], src[m], dst[m],
+//   nq, then per query: q, eq, labels[q], src[eq], dst[eq]
+namespace {
+struct CkWriter {
+  uint8_t *buf;
+  int64_t cap, pos = 0;
+  void bytes(const void *p, int64_t n) {
+    if (buf && pos + n <= cap) memcpy(buf + pos, p, (size_t)n);
+    pos += n;
+  }
+  void i32(int32_t v) { bytes(&v, 4); }
+  void i64(int64_t v) { bytes(&v, 8); }
+};
+struct CkReader {
+  const uint8_t *buf;
+  int64_t size, pos = 0;
+  bool ok = true;
+  void bytes(void *p, int64_t n) {
+    if (n < 0 || pos + n > size) { ok = false; return; }
+    memcpy(p, buf + pos, (size_t)n);
+    pos += n;
+  }
+  int32_t i32() { int32_t v = 0; bytes(&v, 4); return v; }
+  int64_t i64() { int64_t v = 0; bytes(&v, 8); return v; }
+};
+}  // namespace
+
+int gamma_checkpoint(gamma_ctx *ctx, void *buf, int64_t cap, int64_t *size) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "gamma_checkpoint: no graph loaded");
+  if (ctx->staged) return ctx->fail(GAMMA_ESTATE, "gamma_checkpoint: a batch is staged; commit it first");
+  if (!size || (cap > 0 && !buf)) return ctx->fail(GAMMA_EINVAL, "gamma_checkpoint: null output");
+  cudaSetDevice(ctx->device);
+  CKC(cudaStreamSynchronize(ctx->stream));
+  const int32_t n = ctx->n;
+  std::vector<int32_t> lab(n);
+  std::vector<uint2> adj(n);
+  std::vector<uint32_t> col(ctx->pool_top);
+  CKC(cudaMemcpy(lab.data(), ctx->d_label, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+  CKC(cudaMemcpy(adj.data(), ctx->d_adj, sizeof(uint2) * n, cudaMemcpyDeviceToHost));
+  if (ctx->pool_top) CKC(cudaMemcpy(col.data(), ctx->d_col, sizeof(uint32_t) * ctx->pool_top, cudaMemcpyDeviceToHost));
+  const uint32_t idmask = ctx->gd().idmask;
+  std::vector<int32_t> es, ed;  // each undirected edge once, from its smaller end
+  for (int32_t v = 0; v < n; v++)
+    for (uint32_t i = 0; i < adj[v].y; i++) {
+      const int32_t u = (int32_t)((col[adj[v].x + i] >> 1) & idmask);
+      if (v < u) { es.push_back(v); ed.push_back(u); }
+    }
+  CkWriter w{reinterpret_cast<uint8_t *>(buf), cap};
+  w.bytes("GMCK", 4);
+  w.i32(1);
+  w.i32(n);
+  w.i32(ctx->n_cap);
+  w.i64((int64_t)es.size());
+  w.bytes(lab.data(), 4 * (int64_t)n);
+  w.bytes(es.data(), 4 * (int64_t)es.size());
+  w.bytes(ed.data(), 4 * (int64_t)ed.size());
+  w.i32((int32_t)ctx->queries.size());
+  for (const HostQuery &Q : ctx->queries) {
+    w.i32(Q.q);
+    w.i32((int32_t)Q.edges.size());
+    w.bytes(Q.lab.data(), 4 * (int64_t)Q.q);
+    for (auto &e : Q.edges) w.i32(e.first);
+    for (auto &e : Q.edges) w.i32(e.second);
+  }
+  *size = w.pos;
+  return w.pos > cap ? ctx->fail(GAMMA_EOVERFLOW, "gamma_checkpoint: %lld bytes > cap", (long long)w.pos) : GAMMA_OK;
+}
+
+int gamma_restore(gamma_ctx *ctx, const void *buf, int64_t size) {
+  if (!ctx) return GAMMA_EINVAL;
+  ctx->err.clear();
+  if (!buf || size < 24) return ctx->fail(GAMMA_EINVAL, "gamma_restore: no checkpoint");
+  CkReader r{reinterpret_cast<const uint8_t *>(buf), size};
+  char magic[4];
+  r.bytes(magic, 4);
+  if (memcmp(magic, "GMCK", 4) != 0 || r.i32() != 1) return ctx->fail(GAMMA_EINVAL, "gamma_restore: not a checkpoint");
+  const int32_t n = r.i32(), n_cap = r.i32();
+  const int64_t m = r.i64();
+  if (!r.ok || n <= 0 || n_cap < 0 || m < 0 || m > size) return ctx->fail(GAMMA_EINVAL, "gamma_restore: bad header");
+  std::vector<int32_t> lab(n), es(m), ed(m);
+  r.bytes(lab.data(), 4 * (int64_t)n);
+  r.bytes(es.data(), 4 * m);
+  r.bytes(ed.data(), 4 * m);
+  const int32_t nq = r.i32();
+  if (!r.ok || nq < 0) return ctx->fail(GAMMA_EINVAL, "gamma_restore: truncated checkpoint");
+  std::vector<std::vector<int32_t>> ql(nq), qs(nq), qd(nq);
+  for (int32_t j = 0; j < nq; j++) {
+    const int32_t q = r.i32(), eq = r.i32();
+    if (!r.ok || q < 2 || q > GM_MAXQ || eq < 0 || eq > q * (q - 1) / 2)
+      return ctx->fail(GAMMA_EINVAL, "gamma_restore: bad query %d", j);
+    ql[j].resize(q); qs[j].resize(eq); qd[j].resize(eq);
+    r.bytes(ql[j].data(), 4 * (int64_t)q);
+    r.bytes(qs[j].data(), 4 * (int64_t)eq);
+    r.bytes(qd[j].data(), 4 * (int64_t)eq);
+  }
+  if (!r.ok) return ctx->fail(GAMMA_EINVAL, "gamma_restore: truncated checkpoint");
+  // the graph and queries go through the ordinary validated calls; queries
+  // are registered in their original order, so they get their original ids
+  const int32_t keep_reserve = ctx->n_reserve;
+  ctx->n_reserve = n_cap;
+  int rc = gamma_load_graph(ctx, n, lab.data(), m, es.data(), ed.data());
+  ctx->n_reserve = keep_reserve;
+  if (rc != GAMMA_OK) return rc;
+  for (int32_t j = 0; j < nq; j++) {
+    int32_t qid = -1;
+    rc = gamma_register_query(ctx, (int32_t)ql[j].size(), ql[j].data(), (int32_t)qs[j].size(), qs[j].data(),
+                              qd[j].data(), &qid);
+    if (rc != GAMMA_OK) return rc;
+    if (qid != j) return ctx->fail(GAMMA_ESTATE, "gamma_restore: query %d came back as %d", j, qid);
+  }
+  return GAMMA_OK;
+}
+
 int gamma_reserve_vertices(gamma_ctx *ctx, int32_t n_max) {
   if (!ctx) return GAMMA_EINVAL;
   ctx->err.clear();

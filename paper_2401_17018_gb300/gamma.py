@@ -87,6 +87,8 @@ _SIGS = {
     "gamma_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(gamma_stats)]),
     "gamma_export_adjacency": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
     "gamma_reserve_vertices": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "gamma_checkpoint": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "gamma_restore": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "gamma_add_vertices": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32)]),
     "gamma_vertex_neighbors": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64,
                                               ctypes.POINTER(ctypes.c_int64)]),
@@ -245,6 +247,23 @@ def gamma_export_adjacency(ctx: int, n: int, cap: int):
     return off, nbr[:off[-1]], tag[:off[-1]]
 
 
+def gamma_checkpoint(ctx: int) -> bytes:
+    """The committed graph and registered queries as bytes."""
+    lib = load_library()
+    need = ctypes.c_int64(0)
+    rc = lib.gamma_checkpoint(ctx, None, 0, ctypes.byref(need))
+    if rc not in (GAMMA_OK, GAMMA_EOVERFLOW):
+        _check(ctx, rc)
+    buf = np.zeros(max(int(need.value), 1), np.uint8)
+    _check(ctx, lib.gamma_checkpoint(ctx, _ptr(buf), int(need.value), ctypes.byref(need)))
+    return buf[:need.value].tobytes()
+
+
+def gamma_restore(ctx: int, data: bytes) -> None:
+    buf = np.frombuffer(data, np.uint8).copy()
+    _check(ctx, load_library().gamma_restore(ctx, _ptr(buf), int(buf.size)))
+
+
 def gamma_reserve_vertices(ctx: int, n_max: int) -> None:
     _check(ctx, load_library().gamma_reserve_vertices(ctx, int(n_max)))
 
@@ -376,6 +395,22 @@ class Context:
 
     def reserve_vertices(self, n_max: int):
         gamma_reserve_vertices(self.h, n_max)
+
+    def checkpoint(self) -> bytes:
+        return gamma_checkpoint(self.h)
+
+    def restore(self, data: bytes):
+        gamma_restore(self.h, data)
+        # the query sizes, for the row stride of later applies (queries keep their ids)
+        w = np.frombuffer(data, np.int32)
+        n = int(w[2])
+        m = int(np.frombuffer(data[16:24], np.int64)[0])
+        k = 6 + n + 2 * m
+        self.qsizes = {}
+        for j in range(int(w[k])):
+            q, eq = int(w[k + 1]), int(w[k + 2])
+            self.qsizes[j] = q
+            k += 2 + q + 2 * eq
 
     def add_vertices(self, labels) -> int:
         return gamma_add_vertices(self.h, labels)

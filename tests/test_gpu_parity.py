@@ -685,3 +685,42 @@ def test_server_isolates_an_invalid_request(G):
                 got.append((pos.tolist(), neg.tolist()))
         srv.stop()
     assert bad == len(bad_at) and got == alone
+
+
+def test_checkpoint_and_restore(G):
+    """A checkpoint taken after a commit restores the same graph (adjacency
+    lists equal), the same queries under the same ids and the reserved
+    vertex room; a batch applied after the restore, in the same or a fresh
+    context, gives the counts and rows it gave the first time."""
+    w = I.make_workload("tiny")
+    g = w.graph
+    b1 = I.workload_batch(w, 300, 80, sub=2)
+    cur = I.apply_batch_edges(g.src, g.dst, b1)
+    b2 = I.workload_batch(w, 300, 80, sub=3, pool_start=300, cur=cur)
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)])]
+    with G.Context() as ctx:
+        ctx.reserve_vertices(g.n + 8)
+        ctx.load_graph(g.n, g.labels, g.src, g.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        ctx.apply_batch(b1.op, b1.src, b1.dst, qids)
+        with pytest.raises(G.GammaError):
+            ctx.checkpoint()  # a batch is staged
+        ctx.commit()
+        ck = ctx.checkpoint()
+        adj = ctx.export_adjacency(g.n)
+        pos, neg, r, _ = ctx.apply_batch(b2.op, b2.src, b2.dst, qids, row_capacity=1 << 20)
+        first = (pos.tolist(), neg.tolist(), sorted(map(tuple, r.tolist())))
+        ctx.commit()
+        ctx.restore(ck)
+        for a, c in zip(ctx.export_adjacency(g.n), adj):
+            assert np.array_equal(a, c)
+        pos, neg, r, _ = ctx.apply_batch(b2.op, b2.src, b2.dst, qids, row_capacity=1 << 20)
+        assert (pos.tolist(), neg.tolist(), sorted(map(tuple, r.tolist()))) == first
+        ctx.commit()
+        assert ctx.add_vertices(np.zeros(8, np.int32)) == g.n  # the reserve came back too
+    with G.Context() as ctx2:
+        with pytest.raises(G.GammaError):
+            ctx2.restore(b"GMCK" + bytes(40))
+        ctx2.restore(ck)
+        pos, neg, r, _ = ctx2.apply_batch(b2.op, b2.src, b2.dst, qids, row_capacity=1 << 20)
+        assert (pos.tolist(), neg.tolist(), sorted(map(tuple, r.tolist()))) == first
