@@ -63,3 +63,40 @@ def test_create_without_gpu_fails_cleanly():
     with pytest.raises(gamma.GammaError) as e:
         gamma.Context()
     assert e.value.code == gamma.GAMMA_ECUDA
+
+
+def test_null_handles_are_rejected_without_a_gpu():
+    """Every entry point refuses a null context or server with GAMMA_EINVAL
+    (no device work is attempted, nothing crashes)."""
+    from paper_2401_17018_gb300 import gamma
+    lib = gamma.load_library()
+    E = gamma.GAMMA_EINVAL
+    i64 = ctypes.c_int64(0)
+    i32 = ctypes.c_int32(0)
+    calls = {
+        "gamma_load_graph": (None, 1, None, 0, None, None),
+        "gamma_register_query": (None, 2, None, 1, None, None, ctypes.byref(i32)),
+        "gamma_apply_batch": (None, 0, None, None, None, 0, None, None, None, None),
+        "gamma_apply_batches": (None, 1, None, None, None, None, 0, None, None, None),
+        "gamma_fetch_matches": (None, None),
+        "gamma_commit": (None,),
+        "gamma_update_counts": (None, 0, None),
+        "gamma_recount_noalloc": (None, None, None),
+        "gamma_autotune": (None, 0, None, 1, None),
+        "gamma_export_adjacency": (None, None, None, None, 0),
+        "gamma_get_stats": (None, None),
+        "gamma_set_options": (None, None),
+        "gamma_reserve_vertices": (None, 4),
+        "gamma_add_vertices": (None, 1, None, ctypes.byref(i32)),
+        "gamma_vertex_neighbors": (None, 0, None, 0, ctypes.byref(i64)),
+        "gamma_checkpoint": (None, None, 0, ctypes.byref(i64)),
+        "gamma_restore": (None, None, 0),
+        "gamma_server_stats_get": (None, None),
+        "gamma_server_stop": (None,),
+    }
+    for name, args in calls.items():
+        if name not in gamma._SIGS:
+            continue
+        assert getattr(lib, name)(*args) == E, name
+    assert lib.gamma_last_error(None) == b"null context"
+    lib.gamma_destroy(None)
