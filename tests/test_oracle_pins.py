@@ -347,3 +347,26 @@ def test_incremental_equals_static_difference_bulk():
                 assert _is_valid_row(r, q, g.labels, ge, g2e, b)
             checked += len(tup)
     assert checked > 5000
+
+
+def test_multi_query_oracle_with_samples_and_budgets():
+    """bdsm_multi, which the full-size GPU tests use, against single-query
+    runs: all queries at once give the same per-update charges; a sample of
+    updates gives those updates' charges; with a per-(query, update) budget
+    every pair it finishes is exact and the rest are marked NOT_COMPUTED."""
+    w = I.make_workload("tiny")
+    g = w.graph
+    b = I.workload_batch(w, 300, 100, sub=9)
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)]),
+          I.pattern_query([1, 1, 2, 2], [(0, 1), (1, 2), (2, 3), (3, 0)])]
+    single = np.stack([O.bdsm(g.n, g.labels, g.src, g.dst, q, b)[0] for q in qs])
+    multi = O.bdsm_multi(g.n, g.labels, g.src, g.dst, qs, b)
+    assert np.array_equal(multi, single) and int(single.sum()) > 0
+    ev = np.array([3, 17, 18, 150, 399])
+    assert np.array_equal(O.bdsm_multi(g.n, g.labels, g.src, g.dst, qs, b, eval_idx=ev), single[:, ev])
+    tight = O.bdsm_multi(g.n, g.labels, g.src, g.dst, qs, b, update_budget=20)
+    done = tight != O.NOT_COMPUTED
+    assert 0 < done.sum() < done.size
+    assert np.array_equal(tight[done], single[done])
+    loose = O.bdsm_multi(g.n, g.labels, g.src, g.dst, qs, b, update_budget=1 << 40)
+    assert np.array_equal(loose, single)
