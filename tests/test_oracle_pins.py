@@ -370,3 +370,52 @@ def test_multi_query_oracle_with_samples_and_budgets():
     assert np.array_equal(tight[done], single[done])
     loose = O.bdsm_multi(g.n, g.labels, g.src, g.dst, qs, b, update_budget=1 << 40)
     assert np.array_equal(loose, single)
+
+
+def test_incremental_equals_static_difference_property_based():
+    """Property-based form of the O2 = O1 pin: Hypothesis draws the graph
+    (4..9 vertices, 3 labels), the batch (distinct vertex pairs, each an
+    insertion when absent and a deletion when present, in drawn order) and a
+    connected query (random tree plus extra edges, 2..5 vertices)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+
+    @st.composite
+    def case(draw):
+        n = draw(st.integers(4, 9))
+        labels = draw(st.lists(st.integers(0, 2), min_size=n, max_size=n))
+        pairs = [(a, b) for a in range(n) for b in range(a + 1, n)]
+        present = draw(st.lists(st.booleans(), min_size=len(pairs), max_size=len(pairs)))
+        edges = [p for p, x in zip(pairs, present) if x]
+        upd = draw(st.lists(st.sampled_from(pairs), min_size=1, max_size=6, unique=True))
+        flip = draw(st.lists(st.booleans(), min_size=len(upd), max_size=len(upd)))
+        q = draw(st.integers(2, 5))
+        qlab = draw(st.lists(st.integers(0, 2), min_size=q, max_size=q))
+        parent = [draw(st.integers(0, i - 1)) for i in range(1, q)]
+        qe = {(parent[i - 1], i) for i in range(1, q)}
+        extra = draw(st.lists(st.tuples(st.integers(0, q - 1), st.integers(0, q - 1)), max_size=3))
+        qe |= {(min(a, b), max(a, b)) for a, b in extra if a != b}
+        return n, labels, edges, upd, flip, qlab, sorted(qe)
+
+    @hyp.settings(max_examples=400, deadline=None, derandomize=True)
+    @hyp.given(case())
+    def check(c):
+        n, labels, edges, upd, flip, qlab, qe = c
+        es = set(edges)
+        op = np.array([-1 if p in es else 1 for p in upd], np.int8)
+        src = np.array([p[1] if f else p[0] for p, f in zip(upd, flip)], np.int32)
+        dst = np.array([p[0] if f else p[1] for p, f in zip(upd, flip)], np.int32)
+        b = I.Batch(op, src, dst)
+        lab = np.array(labels, np.int32)
+        gs = np.array([a for a, _ in edges], np.int32)
+        gd = np.array([x for _, x in edges], np.int32)
+        query = I.pattern_query(qlab, qe)
+        pos, neg, charge = O.brute_bdsm(n, lab, gs, gd, query, b)
+        cnt, tup = O.bdsm(n, lab, gs, gd, query, b, want_tuples=True)
+        assert O.totals(cnt, b.op) == (len(pos), len(neg))
+        assert {(int(r[1]), tuple(int(x) for x in r[2:])) for r in tup} == \
+            {(1, p) for p in pos} | {(-1, p) for p in neg}
+        for r in tup:
+            assert charge[(int(r[1]), tuple(int(x) for x in r[2:]))] == r[0]
+
+    check()
