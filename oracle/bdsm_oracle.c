@@ -26,6 +26,12 @@
  * sign s with index < i.  No filter, no encoding, no reordering: membership is
  * a hash-set lookup.
  *
+ * Edge labels (Sec. II-A: the label function covers edges too): optional.
+ * With them, an embedding must also map every query edge onto a data edge
+ * of the same label; an inserted edge carries the label its update gives, a
+ * deletion removes the edge whatever its label.  Without them every edge
+ * has label 0.
+ *
  * Batch validity (a reading: the paper is silent): a batch is rejected as a
  * whole when any update has an out-of-range id, a self-loop, an op other than
  * +1/-1, repeats an edge already in the batch, inserts an edge present in G
@@ -118,8 +124,10 @@ typedef struct {
   int32_t eq;
   const int32_t *qs, *qd;
   const int32_t *lab;
-  const hmap *gset;   /* edges of G */
+  const hmap *gset;   /* edges of G -> edge label */
   const hmap *bmap;   /* batch edge -> update index */
+  const int32_t *qel; /* query edge labels (NULL: all 0) */
+  const int32_t *uel; /* labels of inserted edges by update (NULL: all 0) */
   const int8_t *op;
   const adj *view;
   int sign;           /* +1 / -1 of the seeding update */
@@ -134,17 +142,28 @@ typedef struct {
   int over_budget;
 } srch;
 
-/* Is data edge (x, y) an edge of the seed's view, and not an update of the
- * seed's sign with a smaller index (charging rule)? */
-static int edge_ok(const srch *S, int32_t x, int32_t y) {
+/* label of the data edge (x, y) as the update k that touches it leaves or
+ * finds it: an insertion's own label, else the label in G */
+static int64_t touched_label(const srch *S, int64_t k, uint64_t key) {
+  if (S->op[k] == 1) return S->uel ? S->uel[k] : 0;
+  int64_t l = 0;
+  hmap_get(S->gset, key, &l);
+  return l;
+}
+
+/* Is data edge (x, y) an edge of the seed's view with label lab, and not an
+ * update of the seed's sign with a smaller index (charging rule)? */
+static int edge_ok(const srch *S, int32_t x, int32_t y, int64_t lab) {
   uint64_t k = ekey(x, y);
   int64_t bi;
   if (hmap_get(S->bmap, k, &bi)) {
     int bs = S->op[bi];
     if (bs != S->sign) return 0;      /* +: deleted edge not in G'; -: inserted edge not in G */
+    if (touched_label(S, bi, k) != lab) return 0;
     return bi >= S->upd;              /* same sign: only later-or-equal updates */
   }
-  return hmap_get(S->gset, k, NULL);  /* untouched edge: in G iff in G' */
+  int64_t l;
+  return hmap_get(S->gset, k, &l) && l == lab;  /* untouched edge: in G iff in G' */
 }
 
 /* every query edge between u and an assigned query vertex maps into the view */
@@ -153,7 +172,7 @@ static int all_edges_ok(const srch *S, int32_t u, int32_t c) {
     int32_t a = S->qs[e], b = S->qd[e], w;
     if (a == u) w = b; else if (b == u) w = a; else continue;
     if (!S->used_q[w]) continue;
-    if (!edge_ok(S, c, S->phi[w])) return 0;
+    if (!edge_ok(S, c, S->phi[w], S->qel ? S->qel[e] : 0)) return 0;
   }
   return 1;
 }
@@ -227,12 +246,15 @@ static int make_order(srch *S, int32_t a, int32_t b) {
 }
 
 /*
- * oracle_bdsm_multi: incremental matches of nq queries for one batch.
+ * oracle_bdsm_multi_el: incremental matches of nq queries for one batch.
  *   graph G: n vertices with labels[n]; m undirected edges (src[e], dst[e])
- *            (duplicates merged; self-loops or bad ids -> OR_EINVAL, bad_index = -1)
+ *            with labels elabel[m] (NULL: all 0); duplicates merged (with a
+ *            different label, or self-loops or bad ids -> OR_EINVAL, bad_index = -1)
  *   queries: query j has qn[j] <= 31 vertices with labels qlab + qlab_off[j],
- *            qe[j] edges (qsrc/qdst + qe_off[j]); each must be connected
- *   batch:   b updates (op[k] = +1/-1, usrc[k], udst[k])
+ *            qe[j] edges (qsrc/qdst + qe_off[j]) with labels qelabel + qe_off[j]
+ *            (NULL: all 0); each must be connected
+ *   batch:   b updates (op[k] = +1/-1, usrc[k], udst[k]); an insertion's edge
+ *            gets label uelabel[k] (NULL: 0), a deletion ignores it
  *   eval:    n_eval update indices to evaluate (eval_idx == NULL: all b, in order)
  *   out_count[j * ne + i]: matches of query j charged to update eval_idx[i]
  *   tuples:  (one query only) rows of (update, sign, phi[0..q-1]) up to tuple_cap
@@ -244,13 +266,13 @@ static int make_order(srch *S, int32_t a, int32_t b) {
  *            ("not computed") and the next one starts afresh
  * Returns OR_OK, OR_EINVAL (bad_index = offending update), OR_EBUDGET, OR_ENOMEM.
  */
-int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
-                      int32_t nq, const int32_t *qn, const int32_t *qlab, const int64_t *qlab_off,
-                      const int32_t *qe, const int32_t *qsrc, const int32_t *qdst, const int64_t *qe_off,
-                      int64_t b, const int8_t *op, const int32_t *usrc, const int32_t *udst,
-                      int64_t n_eval, const int64_t *eval_idx, uint64_t *out_count,
-                      int32_t *tuples, int64_t tuple_cap, int64_t *n_tuples,
-                      uint64_t node_budget, uint64_t update_budget, int64_t *bad_index) {
+int oracle_bdsm_multi_el(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
+                         const int32_t *elabel, int32_t nq, const int32_t *qn, const int32_t *qlab,
+                         const int64_t *qlab_off, const int32_t *qe, const int32_t *qsrc, const int32_t *qdst,
+                         const int64_t *qe_off, const int32_t *qelabel, int64_t b, const int8_t *op,
+                         const int32_t *usrc, const int32_t *udst, const int32_t *uelabel, int64_t n_eval,
+                         const int64_t *eval_idx, uint64_t *out_count, int32_t *tuples, int64_t tuple_cap,
+                         int64_t *n_tuples, uint64_t node_budget, uint64_t update_budget, int64_t *bad_index) {
   if (bad_index) *bad_index = -1;
   if (n_tuples) *n_tuples = 0;
   if (nq < 0 || (tuples && nq != 1)) return OR_EINVAL;
@@ -271,7 +293,14 @@ int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t
     if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n || src[e] == dst[e]) {
       hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd); return OR_EINVAL;
     }
-    if (hmap_put(&gset, ekey(src[e], dst[e]), 0)) { gs[mu] = src[e]; gd[mu] = dst[e]; mu++; }
+    const int64_t el = elabel ? elabel[e] : 0;
+    if (hmap_put(&gset, ekey(src[e], dst[e]), el)) {
+      gs[mu] = src[e]; gd[mu] = dst[e]; mu++;
+    } else {
+      int64_t had = 0;
+      hmap_get(&gset, ekey(src[e], dst[e]), &had);
+      if (had != el) { hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd); return OR_EINVAL; }
+    }
   }
   /* batch validation, in index order */
   for (int64_t k = 0; k < b; k++) {
@@ -312,6 +341,7 @@ int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t
     S.q = qn[j]; S.qlab = qlab + qlab_off[j]; S.eq = qe[j];
     S.qs = qsrc + qe_off[j]; S.qd = qdst + qe_off[j]; S.lab = labels;
     S.gset = &gset; S.bmap = &bmap; S.op = op; S.budget = node_budget;
+    S.qel = qelabel ? qelabel + qe_off[j] : NULL; S.uel = uelabel;
     S.tuples = tuples; S.tuple_cap = tuple_cap; S.n_tuples = n_tuples;
     for (int64_t i = 0; i < ne && rc == OR_OK; i++) {
       int64_t k = eval_idx ? eval_idx[i] : i;
@@ -324,6 +354,7 @@ int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t
           int32_t a = S.qs[e], bq = S.qd[e];
           int32_t x = o ? udst[k] : usrc[k], y = o ? usrc[k] : udst[k];
           if (labels[x] != S.qlab[a] || labels[y] != S.qlab[bq]) continue;
+          if (touched_label(&S, k, ekey(x, y)) != (S.qel ? S.qel[e] : 0)) continue;
           if (!make_order(&S, a, bq)) { rc = OR_EINVAL; break; }
           memset(S.used_q, 0, sizeof(S.used_q));
           S.phi[a] = x; S.phi[bq] = y; S.used_q[a] = S.used_q[bq] = 1;
@@ -338,6 +369,19 @@ int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t
   adj_free(&AG); adj_free(&AP);
   hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd);
   return rc;
+}
+
+/* Vertex labels only: every edge has label 0. */
+int oracle_bdsm_multi(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
+                      int32_t nq, const int32_t *qn, const int32_t *qlab, const int64_t *qlab_off,
+                      const int32_t *qe, const int32_t *qsrc, const int32_t *qdst, const int64_t *qe_off,
+                      int64_t b, const int8_t *op, const int32_t *usrc, const int32_t *udst,
+                      int64_t n_eval, const int64_t *eval_idx, uint64_t *out_count,
+                      int32_t *tuples, int64_t tuple_cap, int64_t *n_tuples,
+                      uint64_t node_budget, uint64_t update_budget, int64_t *bad_index) {
+  return oracle_bdsm_multi_el(n, labels, m, src, dst, NULL, nq, qn, qlab, qlab_off, qe, qsrc, qdst, qe_off, NULL, b,
+                              op, usrc, udst, NULL, n_eval, eval_idx, out_count, tuples, tuple_cap, n_tuples,
+                              node_budget, update_budget, bad_index);
 }
 
 /* One query: oracle_bdsm_multi with nq = 1. */

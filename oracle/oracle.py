@@ -74,6 +74,14 @@ def _load():
             ctypes.c_int64, p, p,
             p, ctypes.c_int64, p,
             ctypes.c_uint64, ctypes.c_uint64, p]
+        lib.oracle_bdsm_multi_el.restype = ctypes.c_int
+        lib.oracle_bdsm_multi_el.argtypes = [
+            ctypes.c_int32, p, ctypes.c_int64, p, p, p,
+            ctypes.c_int32, p, p, p, p, p, p, p, p,
+            ctypes.c_int64, p, p, p, p,
+            ctypes.c_int64, p, p,
+            p, ctypes.c_int64, p,
+            ctypes.c_uint64, ctypes.c_uint64, p]
         _lib = lib
     return _lib
 
@@ -89,15 +97,25 @@ def _ptr(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _edge_labelled(elabels, queries, batch) -> bool:
+    return (elabels is not None or getattr(batch, "elab", None) is not None or
+            any(getattr(q, "elabels", None) is not None for q in queries))
+
+
 def bdsm(n: int, labels, src, dst, query, batch, eval_idx: Optional[Sequence[int]] = None,
-         want_tuples: bool = False, tuple_cap: int = 1 << 22, budget: int = 0):
+         want_tuples: bool = False, tuple_cap: int = 1 << 22, budget: int = 0, elabels=None):
     """O2: incremental matches of ``query`` for ``batch`` on graph (n, labels, src, dst).
 
     Returns (counts, tuples): counts[j] = matches charged to update eval_idx[j]
     (all updates when eval_idx is None); tuples is an int32 array of rows
     (update, sign, phi[0..q-1]) or None. Raises OracleError on invalid input
-    or when ``budget`` (candidate tests) is exceeded.
+    or when ``budget`` (candidate tests) is exceeded.  Edge labels (Sec. II-A):
+    ``elabels`` for the graph's edges, ``query.elabels`` and ``batch.elab``;
+    absent ones mean label 0.
     """
+    if _edge_labelled(elabels, [query], batch):
+        c, t = _bdsm_el(n, labels, src, dst, [query], batch, eval_idx, want_tuples, tuple_cap, budget, 0, elabels)
+        return c[0], t
     lib = _load()
     labels = np.ascontiguousarray(labels, np.int32)
     src = np.ascontiguousarray(src, np.int32)
@@ -135,12 +153,58 @@ def bdsm(n: int, labels, src, dst, query, batch, eval_idx: Optional[Sequence[int
 NOT_COMPUTED = np.iinfo(np.uint64).max
 
 
+def _bdsm_el(n, labels, src, dst, queries, batch, eval_idx, want_tuples, tuple_cap, budget, update_budget,
+             elabels):
+    """O2 with edge labels: counts [nq, ne] (and rows for a single query)."""
+    lib = _load()
+    labels = np.ascontiguousarray(labels, np.int32)
+    src = np.ascontiguousarray(src, np.int32)
+    dst = np.ascontiguousarray(dst, np.int32)
+    el = None if elabels is None else np.ascontiguousarray(elabels, np.int32)
+    qn = np.array([q.q for q in queries], np.int32)
+    qe = np.array([q.eq for q in queries], np.int32)
+    ql = np.ascontiguousarray(np.concatenate([q.labels for q in queries]), np.int32)
+    qs = np.ascontiguousarray(np.concatenate([q.src for q in queries]), np.int32)
+    qd = np.ascontiguousarray(np.concatenate([q.dst for q in queries]), np.int32)
+    qel = np.ascontiguousarray(np.concatenate([q.elabels if q.elabels is not None else np.zeros(q.eq, np.int32)
+                                               for q in queries]), np.int32)
+    lo = np.concatenate([[0], np.cumsum(qn)[:-1]]).astype(np.int64)
+    eo = np.concatenate([[0], np.cumsum(qe)[:-1]]).astype(np.int64)
+    op = np.ascontiguousarray(batch.op, np.int8)
+    us = np.ascontiguousarray(batch.src, np.int32)
+    ud = np.ascontiguousarray(batch.dst, np.int32)
+    uel = None if batch.elab is None else np.ascontiguousarray(batch.elab, np.int32)
+    b = op.size
+    ev = None if eval_idx is None else np.ascontiguousarray(eval_idx, np.int64)
+    ne = b if ev is None else ev.size
+    counts = np.zeros(max(len(queries) * ne, 1), np.uint64)
+    tup = np.zeros((tuple_cap, 2 + int(qn[0])), np.int32) if want_tuples else None
+    nt = ctypes.c_int64(0)
+    bad = ctypes.c_int64(-1)
+    rc = lib.oracle_bdsm_multi_el(n, _ptr(labels), src.size, _ptr(src), _ptr(dst), _ptr(el),
+                                  len(queries), _ptr(qn), _ptr(ql), _ptr(lo), _ptr(qe), _ptr(qs), _ptr(qd),
+                                  _ptr(eo), _ptr(qel), b, _ptr(op), _ptr(us), _ptr(ud), _ptr(uel),
+                                  ne, _ptr(ev), _ptr(counts), _ptr(tup), tuple_cap if want_tuples else 0,
+                                  ctypes.byref(nt) if want_tuples else None, budget, update_budget,
+                                  ctypes.byref(bad))
+    if rc != OK:
+        raise OracleError(rc, bad.value)
+    counts = counts[:len(queries) * ne].reshape(len(queries), ne)
+    if want_tuples:
+        if nt.value > tuple_cap:
+            raise OracleError(ENOMEM, -1)
+        tup = tup[:nt.value]
+    return counts, tup
+
+
 def bdsm_multi(n: int, labels, src, dst, queries, batch, eval_idx: Optional[Sequence[int]] = None,
-               budget: int = 0, update_budget: int = 0) -> np.ndarray:
+               budget: int = 0, update_budget: int = 0, elabels=None) -> np.ndarray:
     """O2 for several queries in one call (G, G' and the batch map are built
     once). Returns counts[j, i] = matches of query j charged to update eval_idx[i].
     With update_budget, a (query, update) pair needing more candidate tests
     than that is skipped and reported as NOT_COMPUTED."""
+    if queries and _edge_labelled(elabels, queries, batch):
+        return _bdsm_el(n, labels, src, dst, queries, batch, eval_idx, False, 0, budget, update_budget, elabels)[0]
     lib = _load()
     labels = np.ascontiguousarray(labels, np.int32)
     src = np.ascontiguousarray(src, np.int32)
@@ -195,18 +259,23 @@ def _edge(a: int, b: int) -> Tuple[int, int]:
     return (a, b) if a < b else (b, a)
 
 
-def brute_embeddings(n: int, labels, edges: Set[Tuple[int, int]], query) -> Set[Tuple[int, ...]]:
+def brute_embeddings(n: int, labels, edges, query) -> Set[Tuple[int, ...]]:
     """Every injective label-preserving map V(Q) -> V(G) whose query edges are
     all data edges (Def. 2), by trying every data vertex for every query
-    vertex in id order and checking edges as soon as both ends are placed."""
+    vertex in id order and checking edges as soon as both ends are placed.
+    ``edges`` is a set of data edges, or a dict edge -> edge label, in which
+    case every query edge must map onto an edge of its own label (a query
+    without edge labels asks for label 0)."""
     q = query.q
     ql = [int(x) for x in query.labels]
     qe = [(int(a), int(b)) for a, b in zip(query.src, query.dst)]
+    qel = [0] * len(qe) if getattr(query, "elabels", None) is None else [int(x) for x in query.elabels]
     lab = [int(x) for x in labels]
-    nbrs_before = [[] for _ in range(q)]  # query edges (u, w) with w < u
-    for a, b in qe:
+    labelled = isinstance(edges, dict)
+    nbrs_before = [[] for _ in range(q)]  # (w, label) for query edges (u, w) with w < u
+    for (a, b), l in zip(qe, qel):
         hi, lo = max(a, b), min(a, b)
-        nbrs_before[hi].append(lo)
+        nbrs_before[hi].append((lo, l))
     out: Set[Tuple[int, ...]] = set()
     phi = [-1] * q
 
@@ -217,7 +286,8 @@ def brute_embeddings(n: int, labels, edges: Set[Tuple[int, int]], query) -> Set[
         for v in range(n):
             if lab[v] != ql[u] or v in phi[:u]:
                 continue
-            if all(_edge(v, phi[w]) in edges for w in nbrs_before[u]):
+            if all((edges.get(_edge(v, phi[w])) == l) if labelled else (_edge(v, phi[w]) in edges)
+                   for w, l in nbrs_before[u]):
                 phi[u] = v
                 rec(u + 1)
                 phi[u] = -1
@@ -226,19 +296,28 @@ def brute_embeddings(n: int, labels, edges: Set[Tuple[int, int]], query) -> Set[
     return out
 
 
-def brute_bdsm(n: int, labels, src, dst, query, batch):
+def brute_bdsm(n: int, labels, src, dst, query, batch, elabels=None):
     """O1: (positive set, negative set, charge) by static enumeration on G and G'.
 
     charge maps each incremental match (sign, phi) to the lowest index among
-    the same-sign updates whose edge is the image of a query edge.
+    the same-sign updates whose edge is the image of a query edge. With edge
+    labels (``elabels`` for G, ``batch.elab`` for insertions) the graphs are
+    edge -> label maps and embeddings must preserve edge labels too.
     """
-    g = {_edge(int(a), int(b)) for a, b in zip(src, dst)}
     upd: Dict[Tuple[int, int], int] = {}
     for k, (o, a, b) in enumerate(zip(batch.op, batch.src, batch.dst)):
         upd[_edge(int(a), int(b))] = k
     ins = {e for e, k in upd.items() if batch.op[k] > 0}
     dele = {e for e, k in upd.items() if batch.op[k] < 0}
-    gp = (g - dele) | ins
+    if elabels is None and getattr(batch, "elab", None) is None and getattr(query, "elabels", None) is None:
+        g = {_edge(int(a), int(b)) for a, b in zip(src, dst)}
+        gp = (g - dele) | ins
+    else:
+        gl = [0] * len(src) if elabels is None else [int(x) for x in elabels]
+        g = {_edge(int(a), int(b)): l for a, b, l in zip(src, dst, gl)}
+        bl = [0] * len(batch.op) if getattr(batch, "elab", None) is None else [int(x) for x in batch.elab]
+        gp = {e: l for e, l in g.items() if e not in dele}
+        gp.update({e: bl[upd[e]] for e in ins})
     e0 = brute_embeddings(n, labels, g, query)
     e1 = brute_embeddings(n, labels, gp, query)
     pos, neg = e1 - e0, e0 - e1

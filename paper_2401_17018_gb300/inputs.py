@@ -173,13 +173,17 @@ class Batch:
     op: np.ndarray   # int8, +1 insertion, -1 deletion
     src: np.ndarray  # int32
     dst: np.ndarray  # int32
+    # int32 edge labels, None = unlabelled edges; an insertion's label, and
+    # for a deletion the label the edge has (only the inverse batch uses it)
+    elab: Optional[np.ndarray] = None
 
     def __len__(self) -> int:
         return int(self.op.size)
 
     def inverse(self) -> "Batch":
         """The batch that undoes this one (same order, opposite signs)."""
-        return Batch((-self.op).astype(np.int8), self.src.copy(), self.dst.copy())
+        return Batch((-self.op).astype(np.int8), self.src.copy(), self.dst.copy(),
+                     None if self.elab is None else self.elab.copy())
 
 
 def mixed_batch(ins_src, ins_dst, cur_src, cur_dst, n_del: int, seed: int, sub: int) -> Batch:
@@ -218,6 +222,7 @@ class Query:
     src: np.ndarray     # int32 [eq]
     dst: np.ndarray     # int32 [eq]
     kind: str = ""
+    elabels: Optional[np.ndarray] = None  # int32 [eq] edge labels, None = unlabelled edges
 
     @property
     def q(self) -> int:
@@ -228,15 +233,19 @@ class Query:
         return int(self.src.size)
 
     def to_json(self) -> dict:
-        return {"labels": [int(x) for x in self.labels],
-                "edges": [[int(a), int(b)] for a, b in zip(self.src, self.dst)],
-                "kind": self.kind}
+        d = {"labels": [int(x) for x in self.labels],
+             "edges": [[int(a), int(b)] for a, b in zip(self.src, self.dst)],
+             "kind": self.kind}
+        if self.elabels is not None:
+            d["elabels"] = [int(x) for x in self.elabels]
+        return d
 
     @staticmethod
     def from_json(d: dict) -> "Query":
         e = np.array(d["edges"], dtype=np.int32).reshape(-1, 2)
+        el = np.array(d["elabels"], np.int32) if "elabels" in d else None
         return Query(np.array(d["labels"], np.int32), e[:, 0].copy(), e[:, 1].copy(),
-                     d.get("kind", ""))
+                     d.get("kind", ""), el)
 
 
 def random_walk_query(off: np.ndarray, nbr: np.ndarray, labels: np.ndarray, q: int,
@@ -359,10 +368,11 @@ class Graph:
     labels: np.ndarray
     src: np.ndarray
     dst: np.ndarray
+    elabels: Optional[np.ndarray] = None  # int32 edge labels, None = unlabelled edges
 
     def digest(self) -> str:
         h = hashlib.sha256()
-        for a in (self.labels, self.src, self.dst):
+        for a in (self.labels, self.src, self.dst) + (() if self.elabels is None else (self.elabels,)):
             h.update(np.ascontiguousarray(a).tobytes())
         return h.hexdigest()[:16]
 

@@ -419,3 +419,79 @@ def test_incremental_equals_static_difference_property_based():
             assert charge[(int(r[1]), tuple(int(x) for x in r[2:]))] == r[0]
 
     check()
+
+
+def _labelled_case(trial):
+    """A tiny graph with two edge labels, a mixed batch whose insertions carry
+    labels (deletions carry the label the edge has), and edge-labelled queries."""
+    g = I.random_small_graph(7 + trial % 4, 45, 2, 13, trial)
+    r = np.random.default_rng(500 + trial)
+    el = r.integers(0, 2, g.src.size).astype(np.int32)
+    b = _random_batch(g, 700 + trial, 1 + trial % 4, trial % 3)
+    have = {(min(a, c), max(a, c)): l for a, c, l in zip(g.src.tolist(), g.dst.tolist(), el.tolist())}
+    bel = np.array([int(r.integers(0, 2)) if o > 0 else have[(min(a, c), max(a, c))]
+                    for o, a, c in zip(b.op.tolist(), b.src.tolist(), b.dst.tolist())], np.int32)
+    b = I.Batch(b.op, b.src, b.dst, bel)
+    qs = []
+    for q in SMALL_QUERIES + BULK_QUERIES[-2:]:
+        qs.append(I.Query(q.labels, q.src, q.dst, "", r.integers(0, 2, q.eq).astype(np.int32)))
+    return g, el, b, qs
+
+
+def test_edge_labelled_incremental_equals_static_difference():
+    """Edge labels (Sec. II-A: the label function also covers edges): O2 with
+    edge labels equals the edge-labelled static difference on 600 random
+    cases, rows and charges included."""
+    checked = 0
+    for trial in range(600):
+        g, el, b, qs = _labelled_case(trial)
+        if len(b) == 0:
+            continue
+        for q in qs:
+            pos, neg, charge = O.brute_bdsm(g.n, g.labels, g.src, g.dst, q, b, elabels=el)
+            c, tup = O.bdsm(g.n, g.labels, g.src, g.dst, q, b, want_tuples=True, elabels=el)
+            assert O.totals(c, b.op) == (len(pos), len(neg))
+            got = {(int(r[1]), tuple(int(x) for x in r[2:])) for r in tup}
+            assert got == {(1, p) for p in pos} | {(-1, p) for p in neg}
+            for r in tup:
+                assert charge[(int(r[1]), tuple(int(x) for x in r[2:]))] == r[0]
+            checked += len(tup)
+        multi = O.bdsm_multi(g.n, g.labels, g.src, g.dst, qs, b, elabels=el)
+        for j, q in enumerate(qs):
+            assert np.array_equal(multi[j], O.bdsm(g.n, g.labels, g.src, g.dst, q, b, elabels=el)[0])
+    assert checked > 1000
+
+
+def test_edge_labels_reduce_to_vertex_labels():
+    """Closed cases: all edge labels 0 give the unlabelled result; edge labels
+    that are a function of the endpoint labels, asked for by the query with
+    the same function, give the unlabelled result too, and asking one query
+    edge for the other label gives no match at all; a repeated data edge with
+    another label is rejected."""
+    for trial in range(40):
+        g = I.random_small_graph(9, 45, 3, 17, trial)
+        b = _random_batch(g, 900 + trial, 3, 1)
+        f = lambda a, c: int(g.labels[a] + g.labels[c]) % 2  # noqa: E731
+        el = np.array([f(a, c) for a, c in zip(g.src.tolist(), g.dst.tolist())], np.int32)
+        bel = np.array([f(a, c) for a, c in zip(b.src.tolist(), b.dst.tolist())], np.int32)
+        bl = I.Batch(b.op, b.src, b.dst, bel)
+        for q in SMALL_QUERIES:
+            plain = O.bdsm(g.n, g.labels, g.src, g.dst, q, b, want_tuples=True)
+            zero = O.bdsm(g.n, g.labels, g.src, g.dst,
+                          I.Query(q.labels, q.src, q.dst, "", np.zeros(q.eq, np.int32)),
+                          I.Batch(b.op, b.src, b.dst, np.zeros(len(b), np.int32)), want_tuples=True,
+                          elabels=np.zeros(g.src.size, np.int32))
+            assert np.array_equal(plain[0], zero[0]) and np.array_equal(plain[1], zero[1])
+            qf = np.array([int(q.labels[a] + q.labels[c]) % 2 for a, c in zip(q.src.tolist(), q.dst.tolist())],
+                          np.int32)
+            same = O.bdsm(g.n, g.labels, g.src, g.dst, I.Query(q.labels, q.src, q.dst, "", qf), bl,
+                          want_tuples=True, elabels=el)
+            assert np.array_equal(plain[0], same[0]) and np.array_equal(plain[1], same[1])
+            wrong = qf.copy()
+            wrong[0] ^= 1
+            none = O.bdsm(g.n, g.labels, g.src, g.dst, I.Query(q.labels, q.src, q.dst, "", wrong), bl, elabels=el)
+            assert int(none[0].sum()) == 0
+    g = I.Graph(4, np.zeros(4, np.int32), np.array([0, 1, 1], np.int32), np.array([1, 2, 0], np.int32))
+    with pytest.raises(O.OracleError):
+        O.bdsm(g.n, g.labels, g.src, g.dst, SMALL_QUERIES[0], I.Batch(np.ones(1, np.int8),
+               np.array([2], np.int32), np.array([3], np.int32)), elabels=np.array([0, 0, 1], np.int32))
