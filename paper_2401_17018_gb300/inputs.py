@@ -32,6 +32,7 @@ _M2 = U64(0x94D049BB133111EB)
 S_RMAT, S_PERM, S_LABEL, S_SHUF, S_DEL, S_MIX, S_QUERY, S_SIZE, S_ARRIVE = (
     11, 12, 13, 14, 15, 16, 17, 18, 19)
 S_SRV_DEL, S_SRV_INS, S_SRV_MIX = 31, 32, 33
+S_ELABEL = 41
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -127,13 +128,31 @@ def rmat_edges(scale: int, n_edges: int, seed: int,
     return lo, hi
 
 
-def vertex_labels(n: int, n_labels: int, seed: int, zipf_s: Optional[float] = None) -> np.ndarray:
+def vertex_labels(n: int, n_labels: int, seed: int, zipf_s: Optional[float] = None,
+                  stream: int = S_LABEL) -> np.ndarray:
     """iid vertex labels in [0, n_labels): uniform, or Zipf with P(k) ~ (k+1)^-s."""
-    r = rand_u32(seed, S_LABEL, np.arange(n, dtype=U64)).astype(np.int64)
+    r = rand_u32(seed, stream, np.arange(n, dtype=U64)).astype(np.int64)
     if zipf_s is None:
         w = [1.0] * n_labels
     else:
         w = [(k + 1) ** (-zipf_s) for k in range(n_labels)]
+    tot = sum(w)
+    acc, thr = 0.0, []
+    for k in range(n_labels - 1):
+        acc += w[k]
+        thr.append(_prob_threshold(acc / tot))
+    return np.searchsorted(np.array(thr, dtype=np.int64), r, side="right").astype(np.int32)
+
+
+def edge_labels(src: np.ndarray, dst: np.ndarray, n_labels: int, seed: int,
+                zipf_s: Optional[float] = None) -> np.ndarray:
+    """iid labels for undirected edges (the edge-labelled datasets of Table
+    II, e.g. NF and LS), drawn per edge from its canonical (min, max) key so
+    that an edge gets the same label wherever it appears (graph, pool,
+    batch): uniform, or Zipf with P(k) ~ (k+1)^-s."""
+    key = edge_keys(np.asarray(src), np.asarray(dst)).astype(np.uint64)
+    r = (rand_u64(seed, S_ELABEL, key) >> U64(32)).astype(np.int64)
+    w = [1.0] * n_labels if zipf_s is None else [(k + 1) ** (-zipf_s) for k in range(n_labels)]
     tot = sum(w)
     acc, thr = 0.0, []
     for k in range(n_labels - 1):

@@ -106,3 +106,18 @@ def test_extracted_queries_have_their_class(kind):
                     todo.append(v)
         assert len(seen) == nq
     assert got > 0
+
+
+def test_edge_labels_follow_the_edge_not_its_position():
+    w = I.make_workload("mid", scale=12, n_edges=30_000)
+    g = w.graph
+    el = I.edge_labels(g.src, g.dst, 4, 3, 1.2)
+    # same edge, other orientation or position: same label
+    assert np.array_equal(el, I.edge_labels(g.dst[::-1][::-1], g.src, 4, 3, 1.2))
+    perm = np.random.default_rng(1).permutation(g.src.size)
+    assert np.array_equal(el[perm], I.edge_labels(g.src[perm], g.dst[perm], 4, 3, 1.2))
+    # Zipf(1.2) over 4 labels: label 0 most frequent, every label used
+    h = np.bincount(el, minlength=4)
+    assert h.argmax() == 0 and h.min() > 0 and el.max() < 4
+    u = np.bincount(I.edge_labels(g.src, g.dst, 4, 3), minlength=4) / g.src.size
+    assert np.all(np.abs(u - 0.25) < 0.02)
