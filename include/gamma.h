@@ -218,6 +218,19 @@ GAMMA_API int gamma_vertex_neighbors(gamma_ctx *ctx, int32_t v, int32_t *out, in
 GAMMA_API int gamma_checkpoint(gamma_ctx *ctx, void *buf, int64_t cap, int64_t *size);
 GAMMA_API int gamma_restore(gamma_ctx *ctx, const void *buf, int64_t size);
 
+/* The matching order the library uses when an update is mapped onto query
+ * edge (a, b) (Alg. 1 input pi; Sec. IV-C): pi[0] = a, pi[1] = b, then
+ * repeatedly the unplaced query vertex with the most placed neighbours, then
+ * the higher query degree, then the rarer label in G (label_freq[nlab], the
+ * number of data vertices per label; NULL with nlab = 0 treats all labels
+ * alike), then the smaller id.  out_order[q] receives pi, out_bwd[q] (may be
+ * NULL) the placed-neighbour bit mask of each position.  Host only: needs no
+ * context and no GPU.  GAMMA_EINVAL for a query gamma_register_query would
+ * refuse, or when (a, b) is not one of its edges. */
+GAMMA_API int gamma_plan_order(int32_t q, const int32_t *qlabels, int32_t eq, const int32_t *qsrc,
+                               const int32_t *qdst, int32_t a, int32_t b, int32_t nlab,
+                               const int64_t *label_freq, int32_t *out_order, uint16_t *out_bwd);
+
 /* Timings and sizes of the last apply/commit. */
 GAMMA_API int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out);
 

@@ -1173,6 +1173,43 @@ struct CkReader {
 };
 }  // namespace
 
+int gamma_plan_order(int32_t q, const int32_t *qlabels, int32_t eq, const int32_t *qsrc, const int32_t *qdst,
+                     int32_t a, int32_t b, int32_t nlab, const int64_t *label_freq, int32_t *out_order,
+                     uint16_t *out_bwd) {
+  if (q < 2 || q > GM_MAXQ || eq < 1 || !qlabels || !qsrc || !qdst || !out_order || a < 0 || a >= q || b < 0 ||
+      b >= q || a == b || nlab < 0 || (nlab > 0 && !label_freq))
+    return GAMMA_EINVAL;
+  HostQuery Q;
+  Q.q = q;
+  Q.lab.assign(qlabels, qlabels + q);
+  std::vector<std::vector<char>> adjq(q, std::vector<char>(q, 0));
+  for (int32_t e = 0; e < eq; e++) {
+    const int32_t u = qsrc[e], w = qdst[e];
+    if (u < 0 || u >= q || w < 0 || w >= q || u == w || adjq[u][w]) return GAMMA_EINVAL;
+    adjq[u][w] = adjq[w][u] = 1;
+    Q.edges.push_back({u, w});
+  }
+  if (!adjq[a][b]) return GAMMA_EINVAL;
+  // connected (as gamma_register_query requires), so every step of the order has a choice
+  std::vector<char> seen(q, 0);
+  std::vector<int> stack = {0};
+  seen[0] = 1;
+  while (!stack.empty()) {
+    const int u = stack.back();
+    stack.pop_back();
+    for (int w = 0; w < q; w++) if (adjq[u][w] && !seen[w]) { seen[w] = 1; stack.push_back(w); }
+  }
+  for (int u = 0; u < q; u++) if (!seen[u]) return GAMMA_EINVAL;
+  std::vector<int64_t> freq(label_freq, label_freq + nlab);
+  Plan P;
+  make_plan(Q, 0, a, b, freq, P);
+  for (int32_t l = 0; l < q; l++) {
+    out_order[l] = P.qv[l];
+    if (out_bwd) out_bwd[l] = P.bwd[l];
+  }
+  return GAMMA_OK;
+}
+
 int gamma_checkpoint(gamma_ctx *ctx, void *buf, int64_t cap, int64_t *size) {
   if (!ctx) return GAMMA_EINVAL;
   ctx->err.clear();

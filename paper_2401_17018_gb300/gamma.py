@@ -87,6 +87,8 @@ _SIGS = {
     "gamma_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(gamma_stats)]),
     "gamma_export_adjacency": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64]),
     "gamma_reserve_vertices": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "gamma_plan_order": (ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32, _P, _P, _P]),
     "gamma_checkpoint": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "gamma_restore": (ctypes.c_int, [_P, _P, ctypes.c_int64]),
     "gamma_add_vertices": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32)]),
@@ -262,6 +264,21 @@ def gamma_checkpoint(ctx: int) -> bytes:
 def gamma_restore(ctx: int, data: bytes) -> None:
     buf = np.frombuffer(data, np.uint8).copy()
     _check(ctx, load_library().gamma_restore(ctx, _ptr(buf), int(buf.size)))
+
+
+def gamma_plan_order(labels, src, dst, a: int, b: int, label_freq=None):
+    """(order, backward masks) of the matching order for seeded query edge (a, b); no GPU needed."""
+    lab = _as(labels, np.int32)
+    s = _as(src, np.int32)
+    d = _as(dst, np.int32)
+    freq = None if label_freq is None else np.ascontiguousarray(label_freq, np.int64)
+    order = np.zeros(len(lab), np.int32)
+    bwd = np.zeros(len(lab), np.uint16)
+    rc = load_library().gamma_plan_order(int(len(lab)), _ptr(lab), int(len(s)), _ptr(s), _ptr(d), int(a), int(b),
+                                         0 if freq is None else int(freq.size), _ptr(freq), _ptr(order), _ptr(bwd))
+    if rc != GAMMA_OK:
+        raise GammaError(rc, "gamma_plan_order: invalid query or seeded edge")
+    return order, bwd
 
 
 def gamma_reserve_vertices(ctx: int, n_max: int) -> None:
