@@ -1,7 +1,10 @@
 // gm_api.cu -- the C-ABI of libgamma (include/gamma.h): context and state
 // machine, host planner (matching orders, Alg. 1 input pi), buffer management
 // and the launch sequence of one batch: stage -> seed -> DFS with row
-// compaction -> counts to the host; commit separately.
+// compaction -> counts to the host; commit separately.  Also here: several
+// requests staged together (gamma_apply_batches), the apply recorded once as
+// a CUDA graph and replayed (GAMMA_F_GRAPH), the autotuner, vertex additions,
+// and checkpoint / restore through the ordinary load and register calls.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
