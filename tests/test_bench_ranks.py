@@ -1,4 +1,4 @@
-"""The multi-rank path of bench.py on the CPU (gloo, world size 2).
+"""bench.py on the CPU: the multi-rank path (gloo, world size 2) and the reference arm.
 
 The path does not shard: every rank is an independent replica of the whole
 workload, so the only cross-rank step is the maximum of the timed seconds,
@@ -53,3 +53,25 @@ def test_ranks_agree_on_the_slowest_time_and_the_job_rate():
 def test_single_rank_needs_no_collective():
     assert bench.max_over_ranks(3.0) == 3.0
     assert bench.whole_job_rate(100, 1, 4.0) == 25.0
+
+
+def test_reference_arm_prints_one_complete_line():
+    """`bench.py --impl reference` (the oracle on host cores) prints one JSON
+    line with the contract's keys; it needs no GPU."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload", "tiny",
+                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [x for x in out.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert "workload" in d["config"]
