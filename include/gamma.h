@@ -69,8 +69,14 @@ typedef struct {
   uint32_t flags;        /* GAMMA_F_* */
   uint64_t work_budget;  /* max 32-candidate expansion steps per apply; 0 = unlimited */
   int warps_per_block;   /* DFS kernel warps per block (1..16); 0 = 8 */
-  int frontier_tile;     /* partial matches buffered per DFS level per warp (32..256); 0 = 64 */
+  int frontier_tile;     /* partial matches buffered per DFS level per warp (32..4096); 0 = 64 */
   int steal_grain;       /* level-2 candidates per work item; 0 = 64 */
+  /* Bounded waits of the DFS kernel's work donation (an expired wait ends the
+   * apply with GAMMA_ETIMEOUT, counts incomplete, the context still usable): */
+  uint32_t idle_limit_us;    /* longest an idle warp waits for donated work while
+                                others still hold some; 0 = 60 s */
+  uint32_t handoff_limit_us; /* longest a donor waits for a free task slot, or a
+                                receiver for its reserved task; 0 = 1 s */
 } gamma_options;
 
 /* Match rows: row r is rows[r*stride .. r*stride+stride): query id, update
@@ -235,7 +241,8 @@ GAMMA_API int gamma_plan_order(int32_t q, const int32_t *qlabels, int32_t eq, co
 GAMMA_API int gamma_get_stats(gamma_ctx *ctx, gamma_stats *out);
 
 /* Change flags / tuning knobs between batches (fields as in gamma_options;
- * 0 keeps the current value for the three tuning fields). */
+ * 0 keeps the current value for the three tuning fields and the two wait
+ * limits; device and cuda_stream are ignored). */
 GAMMA_API int gamma_set_options(gamma_ctx *ctx, const gamma_options *options);
 
 /* Autotuner for the batched form: one point of the search grid. */
@@ -253,20 +260,30 @@ typedef struct {
 GAMMA_API int gamma_autotune(gamma_ctx *ctx, int32_t npoints, gamma_tune_point *points, int32_t repeats,
                              gamma_tune_point *best);
 
-/* Recount the staged batch without allocating anything: re-runs the DFS
- * kernel over the batch's work items (kept by the last gamma_apply_batch or
- * gamma_apply_batches) and writes the counts to host arrays out_pos / out_neg
- * (nreq * nq entries, laid out as for gamma_apply_batches).  No counterpart in
- * the paper.  It is for callers that must not allocate at that moment, e.g.
- * while recording a CUDA graph in global capture mode or when another
- * allocator owns the device memory: the DFS scratch (task queue, scheduling
- * counters, counts) lives in a static device array of about 1.2 MB that every
- * GPU loading the library holds until exit.  Limits: nreq * nq <= 256
- * (GAMMA_EINVAL beyond), the batched form only (not GAMMA_F_PER_QUERY).  The
- * first call on a device looks up the array's address; make it before any
- * stream capture.  All calls share the array and each clears what must start
- * at zero; calls that overlap on the GPU race and must not be issued. */
-GAMMA_API int gamma_recount_noalloc(gamma_ctx *ctx, uint64_t *out_pos, uint64_t *out_neg);
+/* Recount the staged batch without allocating anything.  No counterpart in
+ * the paper: an operational addition for callers that cannot allocate device
+ * memory at the moment they need the counts -- an application whose device
+ * memory is entirely reserved by another allocator (a framework's caching
+ * allocator or a preallocated arena, where cudaMalloc would fail), or a
+ * latency-critical loop that may not pay for cudaMalloc / cudaFree, which can
+ * synchronize the whole device.  It re-runs the DFS kernel over the work
+ * items the last gamma_apply_batch or gamma_apply_batches kept and writes
+ * the counts to the host arrays out_pos / out_neg, laid out as for
+ * gamma_apply_batches: entry r * nq + j for request r and query j; nreq = 1
+ * after gamma_apply_batch.  cap = entries in each of out_pos / out_neg;
+ * GAMMA_EINVAL when cap < nreq * max(nq, 1), nothing written.  The DFS
+ * scratch (donated-task ring, scheduling counters, count accumulators)
+ * lives in a static device array of about 1.2 MB that every GPU loading the
+ * library holds until the process exits; its limits: nreq * nq <= 256 count
+ * slots (GAMMA_EINVAL beyond) and 16,384 donated-task slots (a donation that
+ * would not fit is not made; the warp keeps the work).  The batched form
+ * only (GAMMA_ESTATE with GAMMA_F_PER_QUERY).  The first call on a device
+ * looks up the array's device address, with that device current, and keeps
+ * it.  All calls share the array, which keeps the last call's contents: each
+ * call clears what must start at zero.  Calls whose GPU work overlaps (from
+ * several threads or contexts at once) race on the array; do not issue
+ * them. */
+GAMMA_API int gamma_recount_noalloc(gamma_ctx *ctx, int32_t cap, uint64_t *out_pos, uint64_t *out_neg);
 
 /* ------------------------------------------------------------------------
  * Served form: a worker thread applies a stream of update requests to the

@@ -62,6 +62,8 @@ struct gamma_ctx {
   uint32_t flags = 0;
   uint64_t budget = 0;
   int wpb = 8, tile = 64, grain = 64;
+  uint64_t idle_ns = 60ull * 1000000000ull;  // bounded waits of the DFS kernel's work donation
+  uint64_t handoff_ns = 1000000000ull;
   int num_sms = 0;
   std::string err;
 
@@ -469,7 +471,8 @@ int enqueue_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_s
   a.sched = ctx->d_sched;
   a.task_seq = ctx->d_task_seq;
   a.task_cap = (uint32_t)ctx->tasks_cap;
-  a.idle_limit_ns = 60ull * 1000000000ull;
+  a.idle_limit_ns = ctx->idle_ns;
+  a.handoff_limit_ns = ctx->handoff_ns;
   a.st = ctx->d_st;
   a.plans = ctx->d_plans; a.nplans = ctx->nplans;
   a.pair_plans = ctx->d_pair_plans;
@@ -734,6 +737,8 @@ int gamma_create(const gamma_options *options, gamma_ctx **out) {
   if (o.warps_per_block > 0) ctx->wpb = o.warps_per_block;
   if (o.frontier_tile > 0) ctx->tile = o.frontier_tile;
   if (o.steal_grain > 0) ctx->grain = o.steal_grain;
+  if (o.idle_limit_us) ctx->idle_ns = 1000ull * o.idle_limit_us;
+  if (o.handoff_limit_us) ctx->handoff_ns = 1000ull * o.handoff_limit_us;
   if (ctx->tile < 32 || ctx->tile > 4096 || ctx->wpb > 16) { delete ctx; return GAMMA_EINVAL; }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, o.device);
   if (o.cuda_stream) {
@@ -816,12 +821,19 @@ int gm_recount_prepare(gamma_ctx *ctx, MatchArgs *a, int *nslots, int *num_sms, 
   m.bkeys = ctx->sb.keys; m.bvals = ctx->sb.vals; m.gstart = ctx->sb.gstart; m.gins = ctx->sb.gins;
   m.n2 = (uint32_t)(2 * ctx->b);
   m.tasks = nullptr; m.sched = nullptr; m.task_seq = nullptr; m.task_cap = 0;
-  m.idle_limit_ns = 60ull * 1000000000ull;
+  m.idle_limit_ns = ctx->idle_ns;
+  m.handoff_limit_ns = ctx->handoff_ns;
   m.st = ctx->d_st;
   return GAMMA_OK;
 }
 
 int gm_ctx_fail(gamma_ctx *ctx, int code, const char *msg) { return ctx->fail(code, "%s", msg); }
+
+// what a recount learned about its DFS launch, for gamma_get_stats
+void gm_recount_done(gamma_ctx *ctx, uint64_t expansions, uint32_t donated) {
+  ctx->stats.expansions = expansions;
+  ctx->stats.donated_tasks = donated;
+}
 
 extern "C" {
 
@@ -835,6 +847,8 @@ int gamma_set_options(gamma_ctx *ctx, const gamma_options *o) {
   if (o->warps_per_block) ctx->wpb = o->warps_per_block;
   if (o->frontier_tile) ctx->tile = o->frontier_tile;
   if (o->steal_grain) ctx->grain = o->steal_grain;
+  if (o->idle_limit_us) ctx->idle_ns = 1000ull * o->idle_limit_us;
+  if (o->handoff_limit_us) ctx->handoff_ns = 1000ull * o->handoff_limit_us;
   ctx->plan_key.clear();
   return GAMMA_OK;
 }

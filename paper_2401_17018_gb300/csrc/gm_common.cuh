@@ -19,6 +19,7 @@
 #define GM_HUB_MIN 128          // list length that makes a vertex a hub at load
 #define GM_EMPTY 0x80000000u    // empty hash slot (keys use at most 31 bits when hashing is on)
 #define GM_FULL 0xffffffffu
+#define GM_MAX_DEVICES 128       // device ordinals the library keeps per-device state for
 
 // ---------------------------------------------------------------------------
 // device status block (one per context, reset at the start of every call)

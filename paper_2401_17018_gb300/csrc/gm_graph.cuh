@@ -66,6 +66,7 @@ struct MatchArgs {
   uint32_t *task_seq;          // [task_cap] 1 once the task in the slot is written
   uint32_t task_cap;
   uint64_t idle_limit_ns;      // longest an idle warp waits for work before flagging an error
+  uint64_t handoff_limit_ns;   // longest a donor waits for a free ring slot, or a receiver for its task
   GmStatus *st;
 };
 

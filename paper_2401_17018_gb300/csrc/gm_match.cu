@@ -23,6 +23,8 @@
 // that neighbour's sorted list), and, below the last level, pass the
 // neighbour-label-count filter.  The last level is only counted (and
 // optionally written out).
+#include <atomic>
+
 #include "gm_graph.cuh"
 
 namespace {
@@ -325,12 +327,28 @@ __device__ bool idle_wait(const MatchArgs &a, uint64_t &slot) {
 }
 
 // lane 0 of a busy warp: reserve n consecutive task numbers and count their
-// future runners as busy.  Task number r lives in ring slot r mod capacity.
+// future runners as busy.  Task number r lives in ring slot r mod capacity,
+// whose previous occupant is task r - capacity; that task is read promptly
+// only if an idle warp already holds its ticket.  So a reservation is refused
+// (false) when its last number would reach capacity past the tickets taken:
+// donors that read the same demand at once could otherwise reserve more
+// tasks than the ring holds and wait on slots nobody is about to free.
 __device__ bool reserve_tasks(const MatchArgs &a, uint32_t n, uint32_t &base) {
   uint32_t *sched = a.sched;
-  if (n > a.task_cap) return false;
-  atomicAdd(sched + GM_SCHED_BUSY, n);
-  base = atomicAdd(sched + GM_SCHED_RESERVE, n);
+  if (n == 0 || n > a.task_cap) return false;
+  atomicAdd(sched + GM_SCHED_BUSY, n);  // the donor itself is busy, so no warp can see zero meanwhile
+  uint32_t r = vload(sched + GM_SCHED_RESERVE);
+  while (true) {
+    const uint32_t t = vload(sched + GM_SCHED_TICKET);
+    if ((int32_t)(r + n - t) > (int32_t)a.task_cap) {
+      atomicSub(sched + GM_SCHED_BUSY, n);
+      return false;
+    }
+    const uint32_t old = atomicCAS(sched + GM_SCHED_RESERVE, r, r + n);
+    if (old == r) break;
+    r = old;
+  }
+  base = r;
   return true;
 }
 
@@ -340,7 +358,7 @@ __device__ bool publish_task(const MatchArgs &a, uint32_t r, const Task &t) {
   const uint32_t ph = r & (a.task_cap - 1u);
   const uint64_t t0 = global_ns();
   while (vload(&a.task_seq[ph]) != 0u) {
-    if (global_ns() - t0 > 1000000000ull) {
+    if (global_ns() - t0 > a.handoff_limit_ns) {
       gm_set_err(a.st, GAMMA_ETIMEOUT);
       atomicExch(&a.st->abort, 1);
       return false;
@@ -406,7 +424,7 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       if (kind == 2) {  // the donor publishes right after reserving; wait for it (bounded)
         const uint64_t t0 = global_ns();
         while (vload(&a.task_seq[slot & (a.task_cap - 1u)]) != (uint32_t)slot + 1u) {
-          if (global_ns() - t0 > 1000000000ull) {
+          if (global_ns() - t0 > a.handoff_limit_ns) {
             gm_set_err(st, GAMMA_ETIMEOUT);
             atomicExch(&st->abort, 1);
             atomicSub(a.sched + GM_SCHED_BUSY, 1u);
@@ -855,10 +873,17 @@ template <bool kCountBytes>
 static int launch_dfs(const MatchArgs &a, int num_sms, cudaStream_t s) {
   const int wpb = a.warps_per_block;
   const size_t smem = smem_per_warp(a.tile, a.nlev) * wpb;
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
+  // the dynamic shared-memory limit is a per-device property of the kernel:
+  // remember, per device ordinal, the largest size already allowed
+  static std::atomic<size_t> configured[GM_MAX_DEVICES];
+  int dev = 0;
+  GM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= GM_MAX_DEVICES) return GAMMA_EINVAL;
+  if (smem > 48 * 1024 && smem > configured[dev].load()) {
     GM_CUDA(cudaFuncSetAttribute(k_dfs<kCountBytes>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
+    size_t prev = configured[dev].load();
+    while (prev < smem && !configured[dev].compare_exchange_weak(prev, smem)) {
+    }
   }
   int per_sm = 0;
   GM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfs<kCountBytes>, wpb * 32, smem));

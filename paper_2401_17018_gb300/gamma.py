@@ -29,7 +29,8 @@ _NAMES = {0: "GAMMA_OK", -1: "GAMMA_EINVAL", -2: "GAMMA_ENOMEM", -3: "GAMMA_ESTA
 class gamma_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("flags", ctypes.c_uint32),
                 ("work_budget", ctypes.c_uint64), ("warps_per_block", ctypes.c_int),
-                ("frontier_tile", ctypes.c_int), ("steal_grain", ctypes.c_int)]
+                ("frontier_tile", ctypes.c_int), ("steal_grain", ctypes.c_int),
+                ("idle_limit_us", ctypes.c_uint32), ("handoff_limit_us", ctypes.c_uint32)]
 
 
 class gamma_matches(ctypes.Structure):
@@ -96,7 +97,7 @@ _SIGS = {
                                               ctypes.POINTER(ctypes.c_int64)]),
     "gamma_set_options": (ctypes.c_int, [_P, ctypes.POINTER(gamma_options)]),
     "gamma_last_error": (ctypes.c_char_p, [_P]),
-    "gamma_recount_noalloc": (ctypes.c_int, [_P, _P, _P]),
+    "gamma_recount_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "gamma_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(gamma_tune_point), ctypes.c_int32,
                                       ctypes.POINTER(gamma_tune_point)]),
     "gamma_server_start": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(gamma_server_options),
@@ -317,19 +318,23 @@ def gamma_last_error(ctx: int) -> str:
 
 # ----------------------------------------------------------- convenience
 def make_options(device: int = 0, stream=None, flags: int = 0, work_budget: int = 0, warps_per_block: int = 0,
-                 frontier_tile: int = 0, steal_grain: int = 0) -> gamma_options:
+                 frontier_tile: int = 0, steal_grain: int = 0, idle_limit_us: int = 0,
+                 handoff_limit_us: int = 0) -> gamma_options:
     s = stream
     if s is not None and hasattr(s, "cuda_stream"):
         s = s.cuda_stream
-    return gamma_options(device, s, flags, work_budget, warps_per_block, frontier_tile, steal_grain)
+    return gamma_options(device, s, flags, work_budget, warps_per_block, frontier_tile, steal_grain, idle_limit_us,
+                         handoff_limit_us)
 
 
 class Context:
     """One libgamma context (see include/gamma.h for the state machine)."""
 
     def __init__(self, device: int = 0, stream=None, flags: int = 0, work_budget: int = 0,
-                 warps_per_block: int = 0, frontier_tile: int = 0, steal_grain: int = 0):
-        self._opts = make_options(device, stream, flags, work_budget, warps_per_block, frontier_tile, steal_grain)
+                 warps_per_block: int = 0, frontier_tile: int = 0, steal_grain: int = 0, idle_limit_us: int = 0,
+                 handoff_limit_us: int = 0):
+        self._opts = make_options(device, stream, flags, work_budget, warps_per_block, frontier_tile, steal_grain,
+                                  idle_limit_us, handoff_limit_us)
         self.h = gamma_create(self._opts)
         self.b = 0
         self.qsizes = {}
@@ -447,10 +452,14 @@ def gamma_autotune(ctx: int, grid, repeats: int = 1):
 
 
 def gamma_recount_noalloc(ctx: int, nslots: int) -> Tuple[np.ndarray, np.ndarray]:
-    """Counts of the staged batch recomputed without allocating (see gamma.h)."""
-    pos = np.zeros(max(nslots, 1), np.uint64)
-    neg = np.zeros(max(nslots, 1), np.uint64)
-    _check(ctx, load_library().gamma_recount_noalloc(ctx, _ptr(pos), _ptr(neg)))
+    """Counts of the staged batch recomputed without allocating (see gamma.h):
+    nslots = requests x queries of the staged batch.  The output arrays are
+    sized for the library's 256-slot limit and their size is passed along,
+    so a wrong nslots cannot make the library write past them."""
+    cap = 256
+    pos = np.zeros(cap, np.uint64)
+    neg = np.zeros(cap, np.uint64)
+    _check(ctx, load_library().gamma_recount_noalloc(ctx, cap, _ptr(pos), _ptr(neg)))
     return pos[:nslots], neg[:nslots]
 
 

@@ -81,7 +81,7 @@ def test_null_handles_are_rejected_without_a_gpu():
         "gamma_fetch_matches": (None, None),
         "gamma_commit": (None,),
         "gamma_update_counts": (None, 0, None),
-        "gamma_recount_noalloc": (None, None, None),
+        "gamma_recount_noalloc": (None, 1, None, None),
         "gamma_autotune": (None, 0, None, 1, None),
         "gamma_export_adjacency": (None, None, None, None, 0),
         "gamma_get_stats": (None, None),

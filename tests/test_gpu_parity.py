@@ -313,6 +313,45 @@ def test_work_budget_times_out_cleanly(G):
         ctx.commit()
 
 
+def test_idle_wait_limit_times_out_cleanly(G):
+    """The DFS kernel's waits for donated work are bounded: with a 1 us
+    limit, the first warp that runs out of work while others still hold some
+    gives up, the apply returns GAMMA_ETIMEOUT with the batch staged, and the
+    context keeps working (commit, then the inverse batch with the default
+    limit gives the counts of a context that never timed out).  No fault and
+    no hang: the wait ends by its own limit."""
+    w = I.make_workload("large", scale=15, n_edges=300_000)
+    g = w.graph
+    b = I.workload_batch(w, 4000, 1000)
+    inv = b.inverse()
+    off, nbr = I.csr_from_edges(g.n, g.src, g.dst)
+    qs = [I.TRIANGLE_WITH_TAIL]
+    att = 0
+    while len(qs) < 4:
+        q = I.random_walk_query(off, nbr, g.labels, 5, "sparse" if att % 2 else "dense", 17, att)
+        att += 1
+        if q is not None:
+            qs.append(q)
+    with G.Context() as ref:
+        ref.load_graph(g.n, g.labels, g.src, g.dst)
+        rq = [ref.register_query(q.labels, q.src, q.dst) for q in qs]
+        ref.apply_batch(b.op, b.src, b.dst, rq)
+        ref.commit()
+        want = ref.apply_batch(inv.op, inv.src, inv.dst, rq)
+        ref.commit()
+    with G.Context(idle_limit_us=1) as ctx:
+        ctx.load_graph(g.n, g.labels, g.src, g.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        with pytest.raises(G.GammaError) as e:
+            ctx.apply_batch(b.op, b.src, b.dst, qids)
+        assert e.value.code == G.GAMMA_ETIMEOUT
+        ctx.commit()  # the batch was staged before the match phase gave up
+        ctx.set_options(idle_limit_us=60_000_000)
+        got = ctx.apply_batch(inv.op, inv.src, inv.dst, qids)
+        ctx.commit()
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
 def test_graph_mode_replays_and_matches(G):
     """GAMMA_F_GRAPH: the apply is captured once per shape and replayed; counts unchanged."""
     w = I.make_workload("tiny")
