@@ -335,6 +335,15 @@ GAMMA_API int gamma_server_stats_get(gamma_server *s, gamma_server_stats *out);
 /* Finish the queued requests, stop the worker and free the server. */
 GAMMA_API int gamma_server_stop(gamma_server *s);
 
+/* Read bandwidth of device `device` for a working set of `bytes` bytes (at
+ * least 1 MiB): a streaming kernel reads the buffer `reps` times with loads
+ * that bypass L1, best of `trials` timed launches after one warm-up, so a
+ * buffer smaller than L2 measures L2 and a larger one DRAM.  *out_gbs gets
+ * GB/s (1e9 bytes/s).  No counterpart in the paper: it is the denominator of
+ * the roofline of kernels whose working set stays in L2.  Allocates and
+ * frees its buffer; GAMMA_ENOMEM if it cannot. */
+GAMMA_API int gamma_probe_bandwidth(int device, int64_t bytes, int32_t reps, int32_t trials, double *out_gbs);
+
 /* Message for the last error on ctx (never NULL; "" when none). */
 GAMMA_API const char *gamma_last_error(gamma_ctx *ctx);
 

@@ -140,6 +140,7 @@ typedef struct {
   uint64_t nodes, budget;
   int32_t *tuples; int64_t tuple_cap; int64_t *n_tuples;
   int over_budget;
+  int32_t shard, nshards; /* this call enumerates the shard-th of nshards disjoint parts */
 } srch;
 
 /* label of the data edge (x, y) as the update k that touches it leaves or
@@ -192,7 +193,11 @@ static void emit(srch *S) {
 
 static void extend(srch *S, int32_t t) {
   if (S->over_budget) return;
-  if (t == S->q) { emit(S); return; }
+  if (t == S->q) {
+    /* a two-vertex query has no searched position: its match belongs to part 0 */
+    if (t > 2 || S->shard == 0) emit(S);
+    return;
+  }
   int32_t u = S->order[t];
   const adj *A = S->view;
   /* every valid image of u is a view-neighbour of the image of each assigned
@@ -206,6 +211,9 @@ static void extend(srch *S, int32_t t) {
     if (A->off[y + 1] - A->off[y] < A->off[x + 1] - A->off[x]) x = y;
   }
   for (int64_t p = A->off[x]; p < A->off[x + 1]; p++) {
+    /* parts: the first searched position's candidates are dealt round-robin by
+     * their place in the anchor's list, so the parts partition the matches */
+    if (t == 2 && S->nshards > 1 && (p - A->off[x]) % S->nshards != S->shard) continue;
     int32_t c = A->nbr[p];
     if (++S->nodes > S->budget && S->budget) { S->over_budget = 1; return; }
     if (S->lab[c] != S->qlab[u]) continue;
@@ -245,16 +253,114 @@ static int make_order(srch *S, int32_t a, int32_t b) {
   return 1;
 }
 
+/* ---------------- a session: G, the batch and G' built once --------------- */
+typedef struct {
+  int32_t n;
+  int32_t *labels;
+  int64_t b;
+  int8_t *op;
+  int32_t *usrc, *udst, *uel; /* uel NULL: inserted edges have label 0 */
+  hmap gset, bmap;
+  adj AG, AP;
+} oracle_session;
+
+void oracle_session_close(oracle_session *z) {
+  if (!z) return;
+  adj_free(&z->AG); adj_free(&z->AP);
+  hmap_free(&z->gset); hmap_free(&z->bmap);
+  free(z->labels); free(z->op); free(z->usrc); free(z->udst); free(z->uel);
+  free(z);
+}
+
 /*
- * oracle_bdsm_multi_el: incremental matches of nq queries for one batch.
- *   graph G: n vertices with labels[n]; m undirected edges (src[e], dst[e])
- *            with labels elabel[m] (NULL: all 0); duplicates merged (with a
- *            different label, or self-loops or bad ids -> OR_EINVAL, bad_index = -1)
+ * oracle_session_open: validate and build G (n vertices with labels[n]; m
+ * undirected edges (src[e], dst[e]) with labels elabel[m], NULL = all 0;
+ * duplicates merged; a duplicate with a different label, a self-loop or a bad
+ * id -> OR_EINVAL with bad_index = -1), the batch (b updates op[k] = +1/-1,
+ * usrc[k], udst[k]; an insertion's edge gets label uelabel[k], NULL = 0) and
+ * G'.  The arrays are copied; *out receives the session.  OR_EINVAL with
+ * bad_index = the smallest offending update for an invalid batch.
+ */
+int oracle_session_open(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
+                        const int32_t *elabel, int64_t b, const int8_t *op, const int32_t *usrc,
+                        const int32_t *udst, const int32_t *uelabel, oracle_session **out, int64_t *bad_index) {
+  if (bad_index) *bad_index = -1;
+  *out = NULL;
+  oracle_session *z = (oracle_session *)calloc(1, sizeof(oracle_session));
+  if (!z) return OR_ENOMEM;
+  z->n = n; z->b = b;
+  z->labels = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+  z->op = (int8_t *)malloc((size_t)b + 1);
+  z->usrc = (int32_t *)malloc(((size_t)b + 1) * sizeof(int32_t));
+  z->udst = (int32_t *)malloc(((size_t)b + 1) * sizeof(int32_t));
+  if (uelabel) z->uel = (int32_t *)malloc(((size_t)b + 1) * sizeof(int32_t));
+  if (!z->labels || !z->op || !z->usrc || !z->udst || (uelabel && !z->uel)) { oracle_session_close(z); return OR_ENOMEM; }
+  memcpy(z->labels, labels, (size_t)n * sizeof(int32_t));
+  if (b) {
+    memcpy(z->op, op, (size_t)b);
+    memcpy(z->usrc, usrc, (size_t)b * sizeof(int32_t));
+    memcpy(z->udst, udst, (size_t)b * sizeof(int32_t));
+    if (uelabel) memcpy(z->uel, uelabel, (size_t)b * sizeof(int32_t));
+  }
+  if (hmap_init(&z->gset, m) || hmap_init(&z->bmap, b)) { oracle_session_close(z); return OR_ENOMEM; }
+  int32_t *gs = (int32_t *)malloc((size_t)(m + 1) * sizeof(int32_t));
+  int32_t *gd = (int32_t *)malloc((size_t)(m + 1) * sizeof(int32_t));
+  if (!gs || !gd) { free(gs); free(gd); oracle_session_close(z); return OR_ENOMEM; }
+  int64_t mu = 0;
+  for (int64_t e = 0; e < m; e++) {
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n || src[e] == dst[e]) {
+      free(gs); free(gd); oracle_session_close(z); return OR_EINVAL;
+    }
+    const int64_t el = elabel ? elabel[e] : 0;
+    if (hmap_put(&z->gset, ekey(src[e], dst[e]), el)) {
+      gs[mu] = src[e]; gd[mu] = dst[e]; mu++;
+    } else {
+      int64_t had = 0;
+      hmap_get(&z->gset, ekey(src[e], dst[e]), &had);
+      if (had != el) { free(gs); free(gd); oracle_session_close(z); return OR_EINVAL; }
+    }
+  }
+  /* batch validation, in index order */
+  for (int64_t k = 0; k < b; k++) {
+    int32_t x = usrc[k], y = udst[k];
+    int bad = (op[k] != 1 && op[k] != -1) || x < 0 || x >= n || y < 0 || y >= n || x == y;
+    if (!bad) {
+      uint64_t kk = ekey(x, y);
+      int ing = hmap_get(&z->gset, kk, NULL);
+      if (!hmap_put(&z->bmap, kk, k)) bad = 1;
+      else if (op[k] == 1 && ing) bad = 1;
+      else if (op[k] == -1 && !ing) bad = 1;
+    }
+    if (bad) {
+      if (bad_index) *bad_index = k;
+      free(gs); free(gd); oracle_session_close(z); return OR_EINVAL;
+    }
+  }
+  /* G' edge list */
+  int32_t *ps = (int32_t *)malloc((size_t)(mu + b + 1) * sizeof(int32_t));
+  int32_t *pd = (int32_t *)malloc((size_t)(mu + b + 1) * sizeof(int32_t));
+  if (!ps || !pd) { free(ps); free(pd); free(gs); free(gd); oracle_session_close(z); return OR_ENOMEM; }
+  int64_t mp = 0;
+  for (int64_t e = 0; e < mu; e++) {
+    int64_t bi;
+    if (hmap_get(&z->bmap, ekey(gs[e], gd[e]), &bi) && op[bi] == -1) continue;
+    ps[mp] = gs[e]; pd[mp] = gd[e]; mp++;
+  }
+  for (int64_t k = 0; k < b; k++)
+    if (op[k] == 1) { ps[mp] = usrc[k]; pd[mp] = udst[k]; mp++; }
+  int rc = (adj_build(&z->AG, n, mu, gs, gd) || adj_build(&z->AP, n, mp, ps, pd)) ? OR_ENOMEM : OR_OK;
+  free(ps); free(pd); free(gs); free(gd);
+  if (rc) { oracle_session_close(z); return rc; }
+  *out = z;
+  return OR_OK;
+}
+
+/*
+ * oracle_session_eval: incremental matches of nq queries for the session's
+ * batch.
  *   queries: query j has qn[j] <= 31 vertices with labels qlab + qlab_off[j],
  *            qe[j] edges (qsrc/qdst + qe_off[j]) with labels qelabel + qe_off[j]
  *            (NULL: all 0); each must be connected
- *   batch:   b updates (op[k] = +1/-1, usrc[k], udst[k]); an insertion's edge
- *            gets label uelabel[k] (NULL: 0), a deletion ignores it
  *   eval:    n_eval update indices to evaluate (eval_idx == NULL: all b, in order)
  *   out_count[j * ne + i]: matches of query j charged to update eval_idx[i]
  *   tuples:  (one query only) rows of (update, sign, phi[0..q-1]) up to tuple_cap
@@ -264,18 +370,21 @@ static int make_order(srch *S, int32_t a, int32_t b) {
  *   update_budget: 0 = none, else each (query, update) evaluation may try that
  *            many candidates; one that needs more gets out_count = UINT64_MAX
  *            ("not computed") and the next one starts afresh
- * Returns OR_OK, OR_EINVAL (bad_index = offending update), OR_EBUDGET, OR_ENOMEM.
+ *   shard, nshards: with nshards > 1, count only the part shard (0-based) of
+ *            each (query, update) evaluation: the candidates of the first
+ *            searched query vertex are dealt round-robin over nshards parts,
+ *            so the parts' counts add up to the whole (nshards <= 1: all)
+ * Returns OR_OK, OR_EINVAL, OR_EBUDGET.
  */
-int oracle_bdsm_multi_el(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
-                         const int32_t *elabel, int32_t nq, const int32_t *qn, const int32_t *qlab,
-                         const int64_t *qlab_off, const int32_t *qe, const int32_t *qsrc, const int32_t *qdst,
-                         const int64_t *qe_off, const int32_t *qelabel, int64_t b, const int8_t *op,
-                         const int32_t *usrc, const int32_t *udst, const int32_t *uelabel, int64_t n_eval,
-                         const int64_t *eval_idx, uint64_t *out_count, int32_t *tuples, int64_t tuple_cap,
-                         int64_t *n_tuples, uint64_t node_budget, uint64_t update_budget, int64_t *bad_index) {
-  if (bad_index) *bad_index = -1;
+int oracle_session_eval(const oracle_session *z, int32_t nq, const int32_t *qn, const int32_t *qlab,
+                        const int64_t *qlab_off, const int32_t *qe, const int32_t *qsrc, const int32_t *qdst,
+                        const int64_t *qe_off, const int32_t *qelabel, int64_t n_eval, const int64_t *eval_idx,
+                        uint64_t *out_count, int32_t *tuples, int64_t tuple_cap, int64_t *n_tuples,
+                        uint64_t node_budget, uint64_t update_budget, int32_t shard, int32_t nshards) {
   if (n_tuples) *n_tuples = 0;
-  if (nq < 0 || (tuples && nq != 1)) return OR_EINVAL;
+  if (!z || nq < 0 || (tuples && nq != 1)) return OR_EINVAL;
+  if (nshards < 1) nshards = 1;
+  if (shard < 0 || shard >= nshards) return OR_EINVAL;
   for (int32_t j = 0; j < nq; j++) {
     int32_t q = qn[j], eq = qe[j];
     const int32_t *qs = qsrc + qe_off[j], *qd = qdst + qe_off[j];
@@ -283,56 +392,9 @@ int oracle_bdsm_multi_el(int32_t n, const int32_t *labels, int64_t m, const int3
     for (int32_t e = 0; e < eq; e++)
       if (qs[e] < 0 || qs[e] >= q || qd[e] < 0 || qd[e] >= q || qs[e] == qd[e]) return OR_EINVAL;
   }
-
-  hmap gset, bmap;
-  if (hmap_init(&gset, m) || hmap_init(&bmap, b)) return OR_ENOMEM;
-  int32_t *gs = (int32_t *)malloc((size_t)(m + 1) * sizeof(int32_t));
-  int32_t *gd = (int32_t *)malloc((size_t)(m + 1) * sizeof(int32_t));
-  int64_t mu = 0;
-  for (int64_t e = 0; e < m; e++) {
-    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n || src[e] == dst[e]) {
-      hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd); return OR_EINVAL;
-    }
-    const int64_t el = elabel ? elabel[e] : 0;
-    if (hmap_put(&gset, ekey(src[e], dst[e]), el)) {
-      gs[mu] = src[e]; gd[mu] = dst[e]; mu++;
-    } else {
-      int64_t had = 0;
-      hmap_get(&gset, ekey(src[e], dst[e]), &had);
-      if (had != el) { hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd); return OR_EINVAL; }
-    }
-  }
-  /* batch validation, in index order */
-  for (int64_t k = 0; k < b; k++) {
-    int32_t x = usrc[k], y = udst[k];
-    int bad = (op[k] != 1 && op[k] != -1) || x < 0 || x >= n || y < 0 || y >= n || x == y;
-    if (!bad) {
-      uint64_t kk = ekey(x, y);
-      int ing = hmap_get(&gset, kk, NULL);
-      if (!hmap_put(&bmap, kk, k)) bad = 1;
-      else if (op[k] == 1 && ing) bad = 1;
-      else if (op[k] == -1 && !ing) bad = 1;
-    }
-    if (bad) {
-      if (bad_index) *bad_index = k;
-      hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd); return OR_EINVAL;
-    }
-  }
-  /* G' edge list */
-  int32_t *ps = (int32_t *)malloc((size_t)(mu + b + 1) * sizeof(int32_t));
-  int32_t *pd = (int32_t *)malloc((size_t)(mu + b + 1) * sizeof(int32_t));
-  int64_t mp = 0;
-  for (int64_t e = 0; e < mu; e++) {
-    int64_t bi;
-    if (hmap_get(&bmap, ekey(gs[e], gd[e]), &bi) && op[bi] == -1) continue;
-    ps[mp] = gs[e]; pd[mp] = gd[e]; mp++;
-  }
-  for (int64_t k = 0; k < b; k++)
-    if (op[k] == 1) { ps[mp] = usrc[k]; pd[mp] = udst[k]; mp++; }
-  adj AG, AP;
-  if (adj_build(&AG, n, mu, gs, gd) || adj_build(&AP, n, mp, ps, pd)) return OR_ENOMEM;
-  free(ps); free(pd);
-
+  const int32_t *labels = z->labels, *usrc = z->usrc, *udst = z->udst;
+  const int8_t *op = z->op;
+  const int64_t b = z->b;
   int rc = OR_OK;
   int64_t ne = eval_idx ? n_eval : b;
   for (int32_t j = 0; j < nq && rc == OR_OK; j++) {
@@ -340,13 +402,14 @@ int oracle_bdsm_multi_el(int32_t n, const int32_t *labels, int64_t m, const int3
     memset(&S, 0, sizeof(S));
     S.q = qn[j]; S.qlab = qlab + qlab_off[j]; S.eq = qe[j];
     S.qs = qsrc + qe_off[j]; S.qd = qdst + qe_off[j]; S.lab = labels;
-    S.gset = &gset; S.bmap = &bmap; S.op = op; S.budget = node_budget;
-    S.qel = qelabel ? qelabel + qe_off[j] : NULL; S.uel = uelabel;
+    S.gset = &z->gset; S.bmap = &z->bmap; S.op = op; S.budget = node_budget;
+    S.qel = qelabel ? qelabel + qe_off[j] : NULL; S.uel = z->uel;
     S.tuples = tuples; S.tuple_cap = tuple_cap; S.n_tuples = n_tuples;
+    S.shard = shard; S.nshards = nshards;
     for (int64_t i = 0; i < ne && rc == OR_OK; i++) {
       int64_t k = eval_idx ? eval_idx[i] : i;
       if (k < 0 || k >= b) { rc = OR_EINVAL; break; }
-      S.sign = op[k]; S.upd = k; S.view = (op[k] == 1) ? &AP : &AG;
+      S.sign = op[k]; S.upd = k; S.view = (op[k] == 1) ? &z->AP : &z->AG;
       S.count = 0;
       if (update_budget) { S.nodes = 0; S.budget = update_budget; S.over_budget = 0; }
       for (int32_t e = 0; e < S.eq; e++) {
@@ -366,8 +429,39 @@ int oracle_bdsm_multi_el(int32_t n, const int32_t *labels, int64_t m, const int3
       if (out_count) out_count[(int64_t)j * ne + i] = (update_budget && S.over_budget) ? UINT64_MAX : S.count;
     }
   }
-  adj_free(&AG); adj_free(&AP);
-  hmap_free(&gset); hmap_free(&bmap); free(gs); free(gd);
+  return rc;
+}
+
+/*
+ * oracle_bdsm_multi_el: one call = open a session, evaluate, close it (the
+ * arguments are those of oracle_session_open and oracle_session_eval, with
+ * the whole search in one part).
+ */
+int oracle_bdsm_multi_el(int32_t n, const int32_t *labels, int64_t m, const int32_t *src, const int32_t *dst,
+                         const int32_t *elabel, int32_t nq, const int32_t *qn, const int32_t *qlab,
+                         const int64_t *qlab_off, const int32_t *qe, const int32_t *qsrc, const int32_t *qdst,
+                         const int64_t *qe_off, const int32_t *qelabel, int64_t b, const int8_t *op,
+                         const int32_t *usrc, const int32_t *udst, const int32_t *uelabel, int64_t n_eval,
+                         const int64_t *eval_idx, uint64_t *out_count, int32_t *tuples, int64_t tuple_cap,
+                         int64_t *n_tuples, uint64_t node_budget, uint64_t update_budget, int64_t *bad_index) {
+  if (n_tuples) *n_tuples = 0;
+  if (nq < 0 || (tuples && nq != 1)) { if (bad_index) *bad_index = -1; return OR_EINVAL; }
+  for (int32_t j = 0; j < nq; j++) {  /* queries are checked before the graph is built */
+    int32_t q = qn[j], eq = qe[j];
+    const int32_t *qs = qsrc + qe_off[j], *qd = qdst + qe_off[j];
+    if (q < 2 || q > 31 || eq < 1) { if (bad_index) *bad_index = -1; return OR_EINVAL; }
+    for (int32_t e = 0; e < eq; e++)
+      if (qs[e] < 0 || qs[e] >= q || qd[e] < 0 || qd[e] >= q || qs[e] == qd[e]) {
+        if (bad_index) *bad_index = -1;
+        return OR_EINVAL;
+      }
+  }
+  oracle_session *z = NULL;
+  int rc = oracle_session_open(n, labels, m, src, dst, elabel, b, op, usrc, udst, uelabel, &z, bad_index);
+  if (rc != OR_OK) return rc;
+  rc = oracle_session_eval(z, nq, qn, qlab, qlab_off, qe, qsrc, qdst, qe_off, qelabel, n_eval, eval_idx, out_count,
+                           tuples, tuple_cap, n_tuples, node_budget, update_budget, 0, 1);
+  oracle_session_close(z);
   return rc;
 }
 

@@ -74,6 +74,17 @@ def _load():
             ctypes.c_int64, p, p,
             p, ctypes.c_int64, p,
             ctypes.c_uint64, ctypes.c_uint64, p]
+        lib.oracle_session_open.restype = ctypes.c_int
+        lib.oracle_session_open.argtypes = [
+            ctypes.c_int32, p, ctypes.c_int64, p, p, p,
+            ctypes.c_int64, p, p, p, p, ctypes.POINTER(ctypes.c_void_p), p]
+        lib.oracle_session_eval.restype = ctypes.c_int
+        lib.oracle_session_eval.argtypes = [
+            p, ctypes.c_int32, p, p, p, p, p, p, p, p,
+            ctypes.c_int64, p, p, p, ctypes.c_int64, p,
+            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32]
+        lib.oracle_session_close.restype = None
+        lib.oracle_session_close.argtypes = [p]
         lib.oracle_bdsm_multi_el.restype = ctypes.c_int
         lib.oracle_bdsm_multi_el.argtypes = [
             ctypes.c_int32, p, ctypes.c_int64, p, p, p,
@@ -231,6 +242,84 @@ def bdsm_multi(n: int, labels, src, dst, queries, batch, eval_idx: Optional[Sequ
     if rc != OK:
         raise OracleError(rc, bad.value)
     return counts[:len(queries) * ne].reshape(len(queries), ne)
+
+
+def _pack_queries(queries):
+    qn = np.array([q.q for q in queries], np.int32)
+    qe = np.array([q.eq for q in queries], np.int32)
+    ql = np.ascontiguousarray(np.concatenate([q.labels for q in queries]), np.int32)
+    qs = np.ascontiguousarray(np.concatenate([q.src for q in queries]), np.int32)
+    qd = np.ascontiguousarray(np.concatenate([q.dst for q in queries]), np.int32)
+    el = None
+    if any(getattr(q, "elabels", None) is not None for q in queries):
+        el = np.ascontiguousarray(np.concatenate([q.elabels if q.elabels is not None else np.zeros(q.eq, np.int32)
+                                                  for q in queries]), np.int32)
+    lo = np.concatenate([[0], np.cumsum(qn)[:-1]]).astype(np.int64)
+    eo = np.concatenate([[0], np.cumsum(qe)[:-1]]).astype(np.int64)
+    return qn, ql, lo, qe, qs, qd, eo, el
+
+
+class Session:
+    """O2 with G, the batch and G' built once and kept (the same program as
+    ``bdsm_multi``, whose every call builds them afresh): for evaluating many
+    (query, update) pairs of one batch, and for splitting one heavy pair over
+    several processes (``part``, ``parts``: the candidates of the first
+    searched query vertex are dealt round-robin, so the parts' counts add up
+    to the whole)."""
+
+    def __init__(self, n: int, labels, src, dst, batch, elabels=None):
+        lib = _load()
+        self._keep = [np.ascontiguousarray(labels, np.int32), np.ascontiguousarray(src, np.int32),
+                      np.ascontiguousarray(dst, np.int32),
+                      None if elabels is None else np.ascontiguousarray(elabels, np.int32),
+                      np.ascontiguousarray(batch.op, np.int8), np.ascontiguousarray(batch.src, np.int32),
+                      np.ascontiguousarray(batch.dst, np.int32),
+                      None if getattr(batch, "elab", None) is None else np.ascontiguousarray(batch.elab, np.int32)]
+        lab, s, d, el, op, us, ud, uel = self._keep
+        self.b = op.size
+        self.op = op
+        h = ctypes.c_void_p()
+        bad = ctypes.c_int64(-1)
+        rc = lib.oracle_session_open(n, _ptr(lab), s.size, _ptr(s), _ptr(d), _ptr(el), op.size, _ptr(op), _ptr(us),
+                                     _ptr(ud), _ptr(uel), ctypes.byref(h), ctypes.byref(bad))
+        if rc != OK:
+            raise OracleError(rc, bad.value)
+        self._h = h
+
+    def eval(self, queries, eval_idx: Optional[Sequence[int]] = None, budget: int = 0, update_budget: int = 0,
+             part: int = 0, parts: int = 1) -> np.ndarray:
+        """counts[j, i] = matches of queries[j] charged to update eval_idx[i]
+        (within part ``part`` of ``parts``); NOT_COMPUTED where update_budget
+        candidate tests did not suffice."""
+        if self._h is None:
+            raise OracleError(EINVAL, -1)
+        qn, ql, lo, qe, qs, qd, eo, el = _pack_queries(queries)
+        ev = None if eval_idx is None else np.ascontiguousarray(eval_idx, np.int64)
+        ne = self.b if ev is None else ev.size
+        counts = np.zeros(max(len(queries) * ne, 1), np.uint64)
+        rc = _load().oracle_session_eval(self._h, len(queries), _ptr(qn), _ptr(ql), _ptr(lo), _ptr(qe), _ptr(qs),
+                                         _ptr(qd), _ptr(eo), _ptr(el), ne, _ptr(ev), _ptr(counts), None, 0, None,
+                                         budget, update_budget, part, parts)
+        if rc != OK:
+            raise OracleError(rc, -1)
+        return counts[:len(queries) * ne].reshape(len(queries), ne)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _load().oracle_session_close(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def totals(counts: np.ndarray, op: np.ndarray, eval_idx=None) -> Tuple[int, int]:

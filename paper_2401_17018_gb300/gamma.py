@@ -98,6 +98,7 @@ _SIGS = {
     "gamma_set_options": (ctypes.c_int, [_P, ctypes.POINTER(gamma_options)]),
     "gamma_last_error": (ctypes.c_char_p, [_P]),
     "gamma_recount_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "gamma_probe_bandwidth": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P]),
     "gamma_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(gamma_tune_point), ctypes.c_int32,
                                       ctypes.POINTER(gamma_tune_point)]),
     "gamma_server_start": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(gamma_server_options),
@@ -461,6 +462,15 @@ def gamma_recount_noalloc(ctx: int, nslots: int) -> Tuple[np.ndarray, np.ndarray
     neg = np.zeros(cap, np.uint64)
     _check(ctx, load_library().gamma_recount_noalloc(ctx, cap, _ptr(pos), _ptr(neg)))
     return pos[:nslots], neg[:nslots]
+
+
+def gamma_probe_bandwidth(device: int, nbytes: int, reps: int = 8, trials: int = 5) -> float:
+    """Read bandwidth (GB/s) for a working set of nbytes (see gamma.h)."""
+    out = ctypes.c_double(0.0)
+    rc = load_library().gamma_probe_bandwidth(int(device), int(nbytes), int(reps), int(trials), ctypes.byref(out))
+    if rc != GAMMA_OK:
+        raise GammaError(rc, "gamma_probe_bandwidth failed")
+    return out.value
 
 
 # ----------------------------------------------------------- served form

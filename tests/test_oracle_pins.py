@@ -495,3 +495,40 @@ def test_edge_labels_reduce_to_vertex_labels():
     with pytest.raises(O.OracleError):
         O.bdsm(g.n, g.labels, g.src, g.dst, SMALL_QUERIES[0], I.Batch(np.ones(1, np.int8),
                np.array([2], np.int32), np.array([3], np.int32)), elabels=np.array([0, 0, 1], np.int32))
+
+
+def _charges_by_update(charge, b):
+    out = np.zeros(len(b), np.uint64)
+    for (_, _phi), k in charge.items():
+        out[k] += 1
+    return out
+
+
+def test_session_and_parts_equal_static_difference():
+    """The oracle session (G, the batch and G' built once, many evaluations)
+    and its split of each (query, update) search into parts: on 300 random
+    small cases, with and without edge labels, the per-update charges of
+    one session equal those of the static difference (O1), and for 2, 3 and
+    7 parts the parts' counts add up to them."""
+    checked = 0
+    for trial in range(300):
+        if trial % 2:
+            g, el, b, qs = _labelled_case(trial)
+        else:
+            n = 6 + trial % 7
+            g = I.random_small_graph(n, 30 + (trial * 7) % 40, 2 + trial % 2, 13, trial)
+            b, el, qs = _random_batch(g, 3000 + trial, 1 + trial % 4, trial % 3), None, BULK_QUERIES
+        if len(b) == 0:
+            continue
+        with O.Session(g.n, g.labels, g.src, g.dst, b, elabels=el) as S:
+            whole = S.eval(qs)
+            for j, q in enumerate(qs):
+                _, _, charge = O.brute_bdsm(g.n, g.labels, g.src, g.dst, q, b, elabels=el)
+                assert np.array_equal(whole[j], _charges_by_update(charge, b))
+                checked += len(charge)
+            for parts in (2, 3, 7):
+                split = [S.eval(qs, part=p, parts=parts) for p in range(parts)]
+                assert np.array_equal(sum(split), whole)
+            ev = np.array([len(b) - 1, 0])
+            assert np.array_equal(S.eval(qs, eval_idx=ev), whole[:, ev])
+    assert checked > 1000
