@@ -4,24 +4,28 @@
 One step = one pass of the whole hot path over one update batch: stage the
 batch into the device-resident dynamic CSR, seed, DFS extension with match
 counting, counts back to the host, commit.
-Steps alternate the batch and its inverse, so the graph cycles between G0
-and G0 + batch and every step does the same amount of work.
 
-Default workload ("mid"): R-MAT scale 20 (a, b, c = .57, .19, .19),
-8,388,608 unique edges of which 90% form G0, 8 vertex labels Zipf(1.2),
-20 six-vertex queries (10 sparse, 10 dense) from tests/golden/queries_mid.json,
-one batch of 90,000 insertions from the held-out pool + 10,000 uniform
-deletions, interleaved. Inputs are synthetic (the paper's datasets are not
-available). The graph (about 60 MB of adjacency) fits in L2, so L2 is flushed
-(a 256 MiB write) before every timed step, outside the timed events.
+Default workload ("large"): R-MAT scale 23 (a, b, c = .57, .19, .19),
+67,108,864 unique edges of which 90% form G0, 16 vertex labels Zipf(1.0),
+8 eight-vertex queries (4 sparse, 4 dense) from tests/golden/queries_large.json,
+five consecutive batches of 800,000 insertions from the held-out pool +
+200,000 uniform deletions from the current graph, each committed before the
+next.  Step k applies batch k mod 5; after the fifth batch G0 is restored
+outside the timed region by applying the five inverse batches in reverse
+order with no queries (stage and commit only).  Workload "mid": R-MAT scale
+20, 8 labels Zipf(1.2), 20 six-vertex queries, one batch of 90,000
+insertions + 10,000 deletions, steps alternating the batch and its inverse.
+Inputs are synthetic (the paper's datasets are not available).  L2 is
+flushed (a 256 MiB write) before every timed step, outside the timed events.
 
-value   = updates/s with the batch already in HBM (device events per step)
+value   = updates/s with the batches already in HBM (device events per step)
 e2e     = the same metric through the C-ABI with host (pinned) batch buffers
 roofline: the DFS kernel's algorithmic bytes (per candidate slot, search
           step, probe and prepared entry; counted by an untimed launch of the
-          instrumented build) / the timed launch's duration, against the
-          measured HBM copy bandwidth
-cpu_baseline: the CPU oracle on a bounded sample of the same batch.
+          instrumented build on the first batch) / that batch's timed DFS
+          duration, against the measured HBM copy bandwidth; the L2 read
+          bandwidth measured by the library's probe kernel is reported beside
+cpu_baseline: the CPU oracle on a bounded sample of the first batch.
 --impl reference times that oracle alone, as the reference arm.
 """
 import argparse
@@ -40,6 +44,8 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOADS = {
+    "large": {"workload": "large", "queries": "tests/golden/queries_large.json", "n_ins": 800_000,
+              "n_del": 200_000, "batches": 5},
     "mid": {"workload": "mid", "queries": "tests/golden/queries_mid.json", "n_ins": 90_000, "n_del": 10_000},
     # the same graph, queries and batch cut to its first 3,000 updates: a case
     # small enough for multi-pass profiler captures
@@ -49,7 +55,25 @@ WORKLOADS = {
     # profiler capture sees the steady state of the full batch
     "mid_20k": {"workload": "mid", "queries": "tests/golden/queries_mid.json", "n_ins": 90_000, "n_del": 10_000,
                 "first": 20000},
+    # the large graph and queries with the first 20,000 updates of its first
+    # batch: a profiling case for the kernel on the large graph
+    "large_20k": {"workload": "large", "queries": "tests/golden/queries_large.json", "n_ins": 800_000,
+                  "n_del": 200_000, "batches": 1, "first": 20000},
     "tiny": {"workload": "tiny", "queries": None, "n_ins": 256, "n_del": 0},
+}
+DESCRIBE = {
+    "large": "R-MAT scale 23, 60.4M edges, 16 labels Zipf(1.0), %d queries of %s vertices, five consecutive "
+             "batches of 1,000,000 updates (800,000 ins + 200,000 del) with a commit after each, one batch per step",
+    "large_20k": "R-MAT scale 23, 60.4M edges, 16 labels Zipf(1.0), %d queries of %s vertices, the first 20,000 "
+                 "updates of the first large batch, batch and inverse alternating",
+    "mid": "R-MAT scale 20, 7.55M edges, 8 labels Zipf(1.2), %d queries of %s vertices, batch of 100,000 updates "
+           "(90,000 ins + 10,000 del), batch and inverse alternating",
+    "mid_3k": "R-MAT scale 20, 7.55M edges, 8 labels Zipf(1.2), %d queries of %s vertices, the first 3,000 updates "
+              "of the mid batch, batch and inverse alternating",
+    "mid_20k": "R-MAT scale 20, 7.55M edges, 8 labels Zipf(1.2), %d queries of %s vertices, the first 20,000 "
+               "updates of the mid batch, batch and inverse alternating",
+    "tiny": "R-MAT scale 11, 9k edges, 4 labels, %d query of %s vertices, 256 insertions, batch and inverse "
+            "alternating",
 }
 METRIC = "updates/s & incremental matches/s per batch (1 GB300); p50/p99 batch latency"
 STATUS_BYTES = 112  # the library's status block, read back after staging, matching and commit
@@ -60,6 +84,9 @@ WORK_BUDGET = 100_000_000_000
 
 
 def load_workload(name):
+    """(workload, queries, timed batches, restore batches): the timed steps
+    cycle through the timed batches; after each full cycle the restore
+    batches (applied untimed, with no queries) bring the graph back to G0."""
     from paper_2401_17018_gb300 import inputs as I
     spec = WORKLOADS[name]
     w = I.make_workload(spec["workload"])
@@ -71,11 +98,16 @@ def load_workload(name):
         queries = [I.Query.from_json(x) for x in qd["queries"]]
     else:
         queries = [I.TRIANGLE_WITH_TAIL]
-    batch = I.workload_batch(w, spec["n_ins"], spec["n_del"])
+    if "batches" in spec:
+        batches = I.consecutive_batches(w, spec["batches"], spec["n_ins"], spec["n_del"])
+    else:
+        batches = [I.workload_batch(w, spec["n_ins"], spec["n_del"])]
     if "first" in spec:
         k = spec["first"]
-        batch = I.Batch(batch.op[:k].copy(), batch.src[:k].copy(), batch.dst[:k].copy())
-    return w, queries, batch
+        batches = [I.Batch(b.op[:k].copy(), b.src[:k].copy(), b.dst[:k].copy()) for b in batches[:1]]
+    if len(batches) == 1:  # the batch and its inverse alternate; both are timed
+        return w, queries, [batches[0], batches[0].inverse()], []
+    return w, queries, batches, [b.inverse() for b in reversed(batches)]
 
 
 class ClockSampler:
@@ -175,97 +207,108 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def dfs_traffic(kernel_file="paper_2401_17018_gb300/csrc/gm_match.cu"):
-    """DRAM bytes per DFS launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "dfs_mid_traffic.json")
+def dfs_traffic(workload, kernel_file="paper_2401_17018_gb300/csrc/gm_match.cu"):
+    """DRAM bytes per DFS launch from the committed ncu summary, if it was
+    taken on this workload and on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "dfs_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     h = hashlib.sha256(open(os.path.join(ROOT, kernel_file), "rb").read()).hexdigest()[:16]
-    if d.get("source_sha") != h:
+    if d.get("source_sha") != h or d.get("workload") != workload:
         return None
     return d.get("dram_bytes_per_launch")
 
 
+def sample_order(n):
+    """A seeded uniform order of the updates of a batch (the CPU samples)."""
+    from paper_2401_17018_gb300 import inputs as I
+    return np.argsort(I.rand_u64(7, 99, np.arange(n, dtype=np.uint64)), kind="stable")
+
+
 def cpu_baseline(w, queries, batch, budget_s=15.0):
     """The oracle, single-threaded, on a sample of the batch's updates (all
-    queries): calls of k uniformly drawn updates each, k doubling while a
-    call's search is short next to its graph build, until about budget_s
-    seconds of search (the sample wraps around the batch when the batch is
-    cheap).  The graph build of a call is measured with empty calls and
-    subtracted."""
+    queries): G, the batch and G' are built once (timed apart and reported,
+    not counted), then updates drawn in a seeded uniform order are evaluated
+    in calls of k updates, k doubling while a call takes under half a second,
+    until about budget_s seconds of search or the whole batch."""
     from oracle import oracle as O
     g = w.graph
-    setup = float("inf")
-    for _ in range(2):
+    t = time.perf_counter()
+    sess = O.Session(g.n, g.labels, g.src, g.dst, batch)
+    build_s = time.perf_counter() - t
+    order = sample_order(len(batch))
+    done, total_s, k = 0, 0.0, 1
+    while total_s < budget_s and done < len(batch):
+        ev = np.sort(order[done:done + k])
         t = time.perf_counter()
-        O.bdsm_multi(g.n, g.labels, g.src, g.dst, queries, batch, eval_idx=[])
-        setup = min(setup, time.perf_counter() - t)
-    order = np.argsort(I_rand(len(batch)))
-    b = len(batch)
-    total_upd, total_s, i, k, calls = 0, 0.0, 0, 2, 0
-    while total_s < budget_s and calls < 5000 and (total_s < 1.0 or total_upd < b):
-        ev = np.sort(order[np.arange(i, i + min(k, b)) % b])
-        i += ev.size
-        t = time.perf_counter()
-        O.bdsm_multi(g.n, g.labels, g.src, g.dst, queries, batch, eval_idx=ev)
-        dt = time.perf_counter() - t - setup
-        total_s += max(dt, 0.0)
-        total_upd += ev.size
-        calls += 1
-        if dt < 4 * setup:
+        sess.eval(queries, eval_idx=ev)
+        dt = time.perf_counter() - t
+        total_s += dt
+        done += ev.size
+        if dt < 0.5:
             k *= 2
-    return {"value": total_upd / max(total_s, 1e-6), "unit": "updates/s", "cores": 1, "kind": "oracle",
-            "sample": "%d updates of the batch drawn uniformly (seeded, wrapping around), all %d queries, single "
-                      "thread, %.2f s of search; graph build (%.3f s per call) excluded" % (
-                          total_upd, len(queries), total_s, setup)}
-
-
-def I_rand(n):
-    from paper_2401_17018_gb300 import inputs as I
-    return I.rand_u64(7, 99, np.arange(n, dtype=np.uint64))
+    sess.close()
+    return {"value": done / max(total_s, 1e-9), "unit": "updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%d updates of the first batch drawn uniformly (seeded), all %d queries, single thread, "
+                      "%.2f s of search; building G, the batch and G' (%.1f s, once) excluded" % (
+                          done, len(queries), total_s, build_s)}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle on the same workload, rank 0 only.
+    Each step evaluates, through one oracle session on G0 and the first
+    batch (built before the timed steps), updates of that batch in a seeded
+    uniform order until the step has searched for about step_s seconds."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import oracle as O
-    w, queries, batch = load_workload(args.workload)
+    w, queries, timed, _ = load_workload(args.workload)
+    batch = timed[0]
     g = w.graph
-    order = np.argsort(I_rand(len(batch)))
-    times, nupd = [], []
+    t = time.perf_counter()
+    sess = O.Session(g.n, g.labels, g.src, g.dst, batch)
+    build_s = time.perf_counter() - t
+    order = sample_order(len(batch))
+    step_s = 1.0
+    times, nupd, pos = [], [], 0
     for step in range(args.warmup + args.steps):
-        ev = np.sort(order[2 * step:2 * step + 2])
-        t = time.perf_counter()
-        O.bdsm_multi(g.n, g.labels, g.src, g.dst, queries, batch, eval_idx=ev)
-        dt = time.perf_counter() - t
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            sess.eval(queries, eval_idx=[int(order[pos % len(batch)])])
+            pos += 1
+            n += 1
+            if time.perf_counter() - t0 >= step_s:
+                break
+        dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
-            nupd.append(ev.size)
+            nupd.append(n)
+    sess.close()
     v = sum(nupd) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic", "config": config_of(args.workload, len(batch), len(queries)),
+            "data": "synthetic", "config": config_of(args.workload, len(batch), queries, len(timed)),
             "cpu_baseline": {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step 2 updates of the batch drawn uniformly (seeded), all %d "
-                                       "queries, graph build included" % len(queries)},
+                             "sample": "per step about %.1f s of single-thread search over updates of the first "
+                                       "batch in a seeded uniform order (%d updates in all), all %d queries; "
+                                       "G, the batch and G' built once before the steps (%.1f s)" % (
+                                           step_s, sum(nupd), len(queries), build_s)},
             "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def config_of(workload, b, nq):
-    spec = WORKLOADS[workload]
-    return {"workload": "%s: R-MAT %s, %d queries, batch %d (%d ins + %d del)" % (
-        workload, {"mid": "scale 20, 7.55M edges, 8 labels Zipf(1.2)",
-                   "mid_3k": "scale 20, 7.55M edges, 8 labels Zipf(1.2), first 3,000 updates of the mid batch",
-                   "mid_20k": "scale 20, 7.55M edges, 8 labels Zipf(1.2), first 20,000 updates of the mid batch",
-                   "tiny": "scale 11, 9k edges, 4 labels"}[workload], nq, b, spec["n_ins"], spec["n_del"]),
-        "batch_updates": b, "queries": nq, "l2": "flushed before every timed step (256 MiB write)",
-        "step": "apply batch (stage+seed+DFS+counts to host) + commit; batch and inverse alternate"}
+def config_of(workload, b, queries, nbatches):
+    sizes = sorted({int(q.labels.size) for q in queries})
+    qdesc = "%d" % sizes[0] if len(sizes) == 1 else "%d..%d" % (sizes[0], sizes[-1])
+    return {"workload": "%s: %s" % (workload, DESCRIBE[workload] % (len(queries), qdesc)),
+            "batch_updates": b, "queries": len(queries), "timed_batches": nbatches,
+            "l2": "flushed before every timed step (256 MiB write)",
+            "step": "apply one batch (stage+seed+DFS+counts to host) + commit"}
 
 
 def run_batched(args):
@@ -454,7 +497,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gamma", choices=["gamma", "reference"])
-    ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-query", action="store_true", help="plain form: one launch sequence per query")
     ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
@@ -486,43 +529,51 @@ def main():
     torch.cuda.set_device(local)
     from paper_2401_17018_gb300 import gamma as G
 
-    w, queries, batch = load_workload(args.workload)
-    inv = batch.inverse()
+    w, queries, timed, restore = load_workload(args.workload)
     g = w.graph
     stream = torch.cuda.Stream()
     flags = G.GAMMA_F_PER_QUERY if args.per_query else 0
     ctx = G.Context(device=local, stream=stream, flags=flags)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     ctx.load_graph(g.n, dev(g.labels), dev(g.src), dev(g.dst))
     qids = [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
-    b = len(batch)
-    d_b = (dev(batch.op), dev(batch.src), dev(batch.dst))
-    d_i = (dev(inv.op), dev(batch.src), dev(batch.dst))
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-    h_b = (pin(batch.op), pin(batch.src), pin(batch.dst))
-    h_i = (pin(inv.op), pin(batch.src), pin(batch.dst))
+    d_timed = [(dev(b.op), dev(b.src), dev(b.dst)) for b in timed]
+    h_timed = [(pin(b.op), pin(b.src), pin(b.dst)) for b in timed]
+    d_restore = [(dev(b.op), dev(b.src), dev(b.dst)) for b in restore]
+    sizes = [len(b) for b in timed]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    cur = [0]  # position in the cycle of timed batches (0: the graph is G0)
 
-    applied = [0]  # batches applied so far: even -> the graph is G0, odd -> G0 + batch
+    def restore_if_cycle_done():
+        if cur[0] == len(timed):
+            for op, s_, d_ in d_restore:  # untimed, no queries: stage and commit only
+                ctx.apply_batch(op, s_, d_, [])
+                ctx.commit()
+            cur[0] = 0
 
-    def step(k, bufs_b, bufs_i):
-        op, s, d = bufs_b if applied[0] % 2 == 0 else bufs_i
-        pos, neg = ctx.apply_batch(op, s, d, qids)
+    def step(bufs):
+        restore_if_cycle_done()
+        k = cur[0]
+        op, s_, d_ = bufs[k]
+        pos, neg = ctx.apply_batch(op, s_, d_, qids)
         st = ctx.stats()
         ctx.commit()
-        applied[0] += 1
-        return int(pos.sum()) + int(neg.sum()), st
+        cur[0] += 1
+        return k, int(pos.sum()) + int(neg.sum()), st
+
+    # instrumented launch (untimed) on the first batch from G0: algorithmic bytes
+    ctx.set_options(flags=flags | G.GAMMA_F_COUNT_BYTES)
+    pos, neg = ctx.apply_batch(*d_timed[0], qids)
+    alg_bytes = ctx.stats()["alg_bytes"]
+    ctx.commit()
+    ctx.set_options(flags=flags)
+    inv0 = timed[0].inverse()
+    ctx.apply_batch(dev(inv0.op), dev(inv0.src), dev(inv0.dst), [])
+    ctx.commit()
 
     for k in range(args.warmup):
-        step(k, d_b, d_i)
-    # instrumented step (untimed): algorithmic bytes of the DFS launch on the batch
-    if applied[0] % 2:
-        step(0, d_b, d_i)
-    ctx.set_options(flags=flags | G.GAMMA_F_COUNT_BYTES)
-    _, st_bytes = step(0, d_b, d_i)
-    step(0, d_b, d_i)
-    ctx.set_options(flags=flags)
-    alg_bytes = st_bytes["alg_bytes"]
+        step(d_timed)
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
@@ -530,63 +581,75 @@ def main():
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    launches0 = ctx.stats()["kernel_launches"]
-    matches, phases = [], []
+    launches = 0
+    matches, phases, which = [], [], []
     t0 = time.perf_counter()
     for k in range(args.steps):
+        restore_if_cycle_done()
+        l0 = ctx.stats()["kernel_launches"]
         with torch.cuda.stream(stream):
             flush.zero_()
             evs[k][0].record(stream)
-        m, st = step(k, d_b, d_i)
+        j, m, st = step(d_timed)
         with torch.cuda.stream(stream):
             evs[k][1].record(stream)
+        launches += ctx.stats()["kernel_launches"] - l0
         matches.append(m)
         phases.append(st)
+        which.append(j)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    launches = ctx.stats()["kernel_launches"] - launches0
     clk = clocks.stop()
     ms = [a.elapsed_time(bb) for a, bb in evs]
+    units = sum(sizes[j] for j in which)
     tot_s = max_over_ranks(sum(ms) / 1e3, dist, "cuda")
     if dist:
         dist.barrier()
 
     # end to end through the C-ABI with host (pinned) batch buffers
-    e2e_t = []
+    e2e_t, e2e_units = [], 0
     for k in range(args.steps):
+        restore_if_cycle_done()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        step(k, h_b, h_i)
+        j, _, _ = step(h_timed)
         e2e_t.append(time.perf_counter() - t)
-    e2e_v = whole_job_rate(b * args.steps, world, max_over_ranks(sum(e2e_t), dist, "cuda"))
+        e2e_units += sizes[j]
+    e2e_v = whole_job_rate(e2e_units, world, max_over_ranks(sum(e2e_t), dist, "cuda"))
 
-    dfs_ms = statistics.mean(p["ms_match"] for p in phases)
+    dfs0 = [p["ms_match"] for p, j in zip(phases, which) if j == 0]
+    dfs_ms = statistics.mean(dfs0) if dfs0 else 0.0
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (dfs_ms / 1e3) / 1e9 if dfs_ms > 0 else 0.0
+    l2_gbs = G.gamma_probe_bandwidth(local, 64 << 20, reps=16, trials=5)
     phase_ms = {k: round(statistics.mean(p[k] for p in phases), 4)
                 for k in ("ms_stage", "ms_seed", "ms_match", "ms_finalize", "ms_commit")}
+    per_batch = {}
+    for m_, j, t_ in zip(matches, which, ms):
+        per_batch.setdefault(j, {"matches": m_, "ms": []})["ms"].append(round(t_, 3))
     line = {
-        "metric": METRIC, "value": whole_job_rate(b * args.steps, world, tot_s), "unit": "updates/s",
+        "metric": METRIC, "value": whole_job_rate(units, world, tot_s), "unit": "updates/s",
         "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": config_of(args.workload, b, len(queries)),
+        "data": "synthetic", "config": config_of(args.workload, sizes[0], queries, len(timed)),
         "matches_per_s": whole_job_rate(sum(matches), world, tot_s),
-        "incremental_matches_per_step": matches[0],
+        "incremental_matches_per_step": sum(matches) / len(matches),
         "p50_ms": statistics.median(ms), "p99_ms": float(np.percentile(ms, 99)), "step_ms": [round(x, 3) for x in ms],
+        "per_batch": {str(j): v for j, v in sorted(per_batch.items())},
         "phase_ms": phase_ms, "wall_s": wall,
-        "e2e": {"value": e2e_v, "unit": "updates/s", "h2d_bytes_per_step": 9 * b,
+        "e2e": {"value": e2e_v, "unit": "updates/s", "h2d_bytes_per_step": 9 * sizes[0],
                 "d2h_bytes_per_step": 16 * len(queries) + 3 * STATUS_BYTES},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": "k_dfs", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": dfs_traffic() if args.workload == "mid" else None,  # recorded on mid only
-                     "peak_kind": peak_kind,
-                     "alg_bytes_per_launch": alg_bytes, "launch_ms": dfs_ms},
+                     "frac": achieved / peak, "traffic": dfs_traffic(args.workload), "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes, "launch_ms": dfs_ms,
+                     "launch": "the DFS launch of the first batch of the cycle",
+                     "l2_read_gbs": l2_gbs, "l2_frac": achieved / l2_gbs if l2_gbs > 0 else None},
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, queries, batch)
+        line["cpu_baseline"] = cpu_baseline(w, queries, timed[0])
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

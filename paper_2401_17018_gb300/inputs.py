@@ -69,20 +69,40 @@ def _prob_threshold(p: float) -> int:
 # graphs
 # --------------------------------------------------------------------------
 
-def rmat_edges(scale: int, n_edges: int, seed: int,
-               a: float = 0.57, b: float = 0.19, c: float = 0.19,
-               permute: bool = True) -> Tuple[np.ndarray, np.ndarray]:
-    """Undirected R-MAT edge list with exactly ``n_edges`` unique edges.
+_RMAT_LIB = None
 
-    Candidates are drawn in index order; self-loops are dropped, each edge is
-    canonicalised to (min, max) and only its first occurrence is kept, until
-    ``n_edges`` unique edges exist. Vertex ids are then relabelled by a seeded
-    random permutation so that hubs are not clustered at low ids. Returns
-    int32 arrays (src < dst), in first-draw order.
-    """
-    n = 1 << scale
-    ta, tab, tabc = (_prob_threshold(a), _prob_threshold(a + b),
-                     _prob_threshold(a + b + c))
+
+def _rmat_lib():
+    """The C version of the R-MAT draw (rmat_gen.c), built with gcc on first
+    use into the package's _build folder; None when it cannot be built."""
+    global _RMAT_LIB
+    if _RMAT_LIB is None:
+        import ctypes
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src = os.path.join(here, "rmat_gen.c")
+        so = os.path.join(here, "_build", "librmat.so")
+        try:
+            if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+                os.makedirs(os.path.dirname(so), exist_ok=True)
+                tmp = so + ".tmp%d" % os.getpid()
+                subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src])
+                os.replace(tmp, so)
+            lib = ctypes.CDLL(so)
+        except (OSError, subprocess.CalledProcessError):
+            _RMAT_LIB = False
+            return None
+        p = ctypes.c_void_p
+        lib.rmat_draw.restype = ctypes.c_int64
+        lib.rmat_draw.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                  ctypes.c_uint32, p, p]
+        _RMAT_LIB = lib
+    return _RMAT_LIB or None
+
+
+def _rmat_draw_numpy(scale: int, n_edges: int, seed: int, ta: int, tab: int, tabc: int):
+    """First ``n_edges`` distinct non-loop candidates in draw order (numpy)."""
     keys_all: List[np.ndarray] = []
     drawn = 0
     need = n_edges
@@ -116,8 +136,38 @@ def rmat_edges(scale: int, n_edges: int, seed: int,
         need = n_edges - uniq.size
     order = np.argsort(first, kind="stable")[:n_edges]
     sel = uniq[order]
-    src = (sel >> 32).astype(np.int64)
-    dst = (sel & 0xFFFFFFFF).astype(np.int64)
+    return (sel >> 32).astype(np.int64), (sel & 0xFFFFFFFF).astype(np.int64)
+
+
+def rmat_edges(scale: int, n_edges: int, seed: int,
+               a: float = 0.57, b: float = 0.19, c: float = 0.19,
+               permute: bool = True, engine: str = "auto") -> Tuple[np.ndarray, np.ndarray]:
+    """Undirected R-MAT edge list with exactly ``n_edges`` unique edges.
+
+    Candidates are drawn in index order; self-loops are dropped, each edge is
+    canonicalised to (min, max) and only its first occurrence is kept, until
+    ``n_edges`` unique edges exist. Vertex ids are then relabelled by a seeded
+    random permutation so that hubs are not clustered at low ids. Returns
+    int32 arrays (src < dst), in first-draw order.  ``engine``: "numpy", "c"
+    (rmat_gen.c, the same bytes, much faster) or "auto" (C when it builds).
+    """
+    n = 1 << scale
+    ta, tab, tabc = (_prob_threshold(a), _prob_threshold(a + b),
+                     _prob_threshold(a + b + c))
+    lib = _rmat_lib() if engine in ("auto", "c") else None
+    if engine == "c" and lib is None:
+        raise RuntimeError("the C R-MAT generator could not be built")
+    if lib is not None:
+        import ctypes
+        s32 = np.empty(n_edges, np.int32)
+        d32 = np.empty(n_edges, np.int32)
+        drawn = lib.rmat_draw(scale, n_edges, int(stream_key(seed, S_RMAT)), ta, tab, tabc,
+                              s32.ctypes.data_as(ctypes.c_void_p), d32.ctypes.data_as(ctypes.c_void_p))
+        if drawn < 0:
+            raise MemoryError("rmat_draw")
+        src, dst = s32.astype(np.int64), d32.astype(np.int64)
+    else:
+        src, dst = _rmat_draw_numpy(scale, n_edges, seed, ta, tab, tabc)
     if permute:
         perm_key = rand_u64(seed, S_PERM, np.arange(n, dtype=U64))
         newid = np.empty(n, dtype=np.int64)
@@ -435,6 +485,41 @@ def workload_batch(w: Workload, n_ins: int, n_del: int, sub: int = 0, pool_start
     cs, cd = cur if cur is not None else (w.graph.src, w.graph.dst)
     return mixed_batch(w.pool_src[pool_start:pool_start + n_ins],
                        w.pool_dst[pool_start:pool_start + n_ins], cs, cd, n_del, w.seed, sub)
+
+
+def consecutive_batches(w: Workload, count: int, n_ins: int, n_del: int) -> List[Batch]:
+    """``count`` batches applied one after another to G0, each committed
+    before the next (the large workload: five batches of 800,000 insertions
+    and 200,000 deletions).  Batch k inserts the pool edges
+    [k * n_ins, (k + 1) * n_ins) and deletes ``n_del`` edges drawn uniformly
+    without replacement from the graph as it stands after batches 0..k-1;
+    its updates are interleaved by a seeded shuffle."""
+    cs, cd = w.graph.src, w.graph.dst
+    out = []
+    for k in range(count):
+        isrc = w.pool_src[k * n_ins:(k + 1) * n_ins]
+        idst = w.pool_dst[k * n_ins:(k + 1) * n_ins]
+        if isrc.size < n_ins or n_del > cs.size:
+            raise ValueError("the pool or the graph is too small for batch %d" % k)
+        pick = sample_distinct(cs.size, n_del, w.seed, S_DEL, 100 + k)
+        op = np.concatenate([np.ones(n_ins, np.int8), -np.ones(n_del, np.int8)])
+        s = np.concatenate([isrc, cs[pick]]).astype(np.int32)
+        d = np.concatenate([idst, cd[pick]]).astype(np.int32)
+        mix = shuffle_order(op.size, w.seed, S_MIX, 100 + k)
+        out.append(Batch(op[mix], s[mix], d[mix]))
+        keep = np.ones(cs.size, bool)
+        keep[pick] = False
+        cs = np.concatenate([cs[keep], np.minimum(isrc, idst)]).astype(np.int32)
+        cd = np.concatenate([cd[keep], np.maximum(isrc, idst)]).astype(np.int32)
+    return out
+
+
+def graph_after(src: np.ndarray, dst: np.ndarray, batches: Sequence[Batch]) -> Tuple[np.ndarray, np.ndarray]:
+    """Edge list after applying ``batches`` in order (each valid on the graph
+    the previous ones leave)."""
+    for b in batches:
+        src, dst = apply_batch_edges(src, dst, b)
+    return src, dst
 
 
 def served_sizes(n_batches: int, seed: int, lo_exp: float = 3.0, hi_exp: float = 6.0) -> np.ndarray:
