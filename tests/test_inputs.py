@@ -121,3 +121,27 @@ def test_edge_labels_follow_the_edge_not_its_position():
     assert h.argmax() == 0 and h.min() > 0 and el.max() < 4
     u = np.bincount(I.edge_labels(g.src, g.dst, 4, 3), minlength=4) / g.src.size
     assert np.all(np.abs(u - 0.25) < 0.02)
+
+
+def test_c_rmat_draw_gives_the_numpy_bytes():
+    """rmat_gen.c is the numpy R-MAT draw in C: the same edge lists, byte for
+    byte, on several scales and seeds (including the tiny workload's graph)."""
+    for scale, ne, seed in [(6, 100, 1), (11, 10_000, 1), (13, 50_000, 4), (15, 200_000, 2)]:
+        a = I.rmat_edges(scale, ne, seed, engine="c")
+        b = I.rmat_edges(scale, ne, seed, engine="numpy")
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_consecutive_batches_are_valid_in_order():
+    """Each of the consecutive batches is valid on the graph the previous ones
+    leave: insertions absent, deletions present, no edge repeated."""
+    w = I.make_workload("large", scale=12, n_edges=40_000)
+    bs = I.consecutive_batches(w, 4, 800, 300)
+    cur = {(int(a), int(b)) for a, b in zip(w.graph.src, w.graph.dst)}
+    for b in bs:
+        keys = [(min(int(x), int(y)), max(int(x), int(y))) for x, y in zip(b.src, b.dst)]
+        assert len(set(keys)) == len(keys) and len(b) == 1100
+        for o, k in zip(b.op, keys):
+            assert (k in cur) == (o < 0)
+        for o, k in zip(b.op, keys):
+            (cur.discard if o < 0 else cur.add)(k)
