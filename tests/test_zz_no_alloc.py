@@ -75,7 +75,8 @@ def test_recount_without_allocation_two_requests(G):
     with G.Context(steal_grain=1) as ctx:
         ctx.load_graph(g.n, g.labels, g.src, g.dst)
         qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
-        pos, neg = ctx.apply_batches(off, op, src, dst, qids)
+        pos, neg = ctx.apply_batches(off, op, src, dst, qids)  # [request, query]
+        pos, neg = pos.reshape(-1), neg.reshape(-1)  # entry r * nq + j, as the recount lays them out
         assert pos.size == 2 * len(qids) and int(pos.sum() + neg.sum()) > 0
         for _ in range(2):
             p2, n2 = G.gamma_recount_noalloc(ctx.h, 2 * len(qids))
