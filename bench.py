@@ -499,6 +499,10 @@ def main():
     ap.add_argument("--impl", default="gamma", choices=["gamma", "reference"])
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hub-min-degree", type=int, default=0, help="lists that get a hash index (0: the library's default)")
+    ap.add_argument("--tile", type=int, default=0, help="DFS frontier tile (0: default)")
+    ap.add_argument("--wpb", type=int, default=0, help="DFS warps per block (0: default)")
+    ap.add_argument("--grain", type=int, default=0, help="level-2 candidates per work item (0: default)")
     ap.add_argument("--per-query", action="store_true", help="plain form: one launch sequence per query")
     ap.add_argument("--mode", default="plain", choices=["plain", "batched", "served"],
                     help="plain: the metric's workload; batched / served: the batched and served forms")
@@ -533,7 +537,8 @@ def main():
     g = w.graph
     stream = torch.cuda.Stream()
     flags = G.GAMMA_F_PER_QUERY if args.per_query else 0
-    ctx = G.Context(device=local, stream=stream, flags=flags)
+    ctx = G.Context(device=local, stream=stream, flags=flags, hub_min_degree=args.hub_min_degree,
+                    frontier_tile=args.tile, warps_per_block=args.wpb, steal_grain=args.grain)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     ctx.load_graph(g.n, dev(g.labels), dev(g.src), dev(g.dst))
@@ -608,7 +613,7 @@ def main():
 
     # end to end through the C-ABI with host (pinned) batch buffers
     e2e_t, e2e_units = [], 0
-    for k in range(args.steps):
+    for k in range(min(args.steps, len(timed))):  # one cycle of the timed batches
         restore_if_cycle_done()
         torch.cuda.synchronize()
         t = time.perf_counter()

@@ -77,6 +77,10 @@ typedef struct {
                                 others still hold some; 0 = 60 s */
   uint32_t handoff_limit_us; /* longest a donor waits for a free task slot, or a
                                 receiver for its reserved task; 0 = 1 s */
+  int32_t hub_min_degree;    /* lists with at least this many entries at load get a
+                                hash index for membership tests (memory: about 12
+                                bytes per entry of such lists); 0 = 128; takes
+                                effect at the next gamma_load_graph */
 } gamma_options;
 
 /* Match rows: row r is rows[r*stride .. r*stride+stride): query id, update

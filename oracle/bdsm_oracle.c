@@ -19,8 +19,9 @@
  * edge, fix phi(a), phi(b) to its endpoints when the labels agree, then
  * backtrack over the other query vertices in a fixed order in which every
  * vertex has an already-assigned query neighbour (the query is connected),
- * trying every V-neighbour of the image of one assigned query neighbour (the
- * one whose image has the fewest view neighbours).  A candidate
+ * trying every V-neighbour carrying the vertex's label of the image of one
+ * assigned query neighbour (the one whose image has the fewest such
+ * neighbours; lists are sorted by label, then id).  A candidate
  * is kept when its label matches, it is not already used, and for EVERY query
  * edge to an assigned vertex the image edge is in V and is not an update of
  * sign s with index < i.  No filter, no encoding, no reordering: membership is
@@ -96,9 +97,37 @@ static uint64_t ekey(int32_t a, int32_t b) {
 }
 
 /* ---------------- adjacency lists (for iteration only) -------------------- */
-typedef struct { int64_t *off; int32_t *nbr; } adj;
+/* Each vertex's neighbours are kept sorted by (label, id), so the neighbours
+ * that carry one label form one run, found by two binary searches. */
+typedef struct { int64_t *off; int32_t *nbr; const int32_t *lab; } adj;
 
-static int adj_build(adj *A, int32_t n, int64_t m, const int32_t *s, const int32_t *d) {
+static const int32_t *g_sort_lab; /* labels for the qsort comparator (single-threaded build) */
+
+static int by_label_then_id(const void *x, const void *y) {
+  const int32_t a = *(const int32_t *)x, b = *(const int32_t *)y;
+  const int32_t la = g_sort_lab[a], lb = g_sort_lab[b];
+  if (la != lb) return la < lb ? -1 : 1;
+  return (a > b) - (a < b);
+}
+
+/* [*lo, *hi) = the run of x's neighbours with label lab */
+static void label_run(const adj *A, int32_t x, int32_t lab, int64_t *lo, int64_t *hi) {
+  int64_t a = A->off[x], b = A->off[x + 1];
+  while (a < b) { /* first neighbour with label >= lab */
+    int64_t m = a + (b - a) / 2;
+    if (A->lab[A->nbr[m]] < lab) a = m + 1; else b = m;
+  }
+  *lo = a;
+  b = A->off[x + 1];
+  while (a < b) { /* first neighbour with label > lab */
+    int64_t m = a + (b - a) / 2;
+    if (A->lab[A->nbr[m]] <= lab) a = m + 1; else b = m;
+  }
+  *hi = a;
+}
+
+static int adj_build(adj *A, int32_t n, int64_t m, const int32_t *s, const int32_t *d, const int32_t *lab) {
+  A->lab = lab;
   A->off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
   A->nbr = (int32_t *)malloc((size_t)(2 * m + 1) * sizeof(int32_t));
   if (!A->off || !A->nbr) return -1;
@@ -112,6 +141,9 @@ static int adj_build(adj *A, int32_t n, int64_t m, const int32_t *s, const int32
     A->nbr[fill[d[e]]++] = s[e];
   }
   free(fill);
+  g_sort_lab = lab;
+  for (int32_t v = 0; v < n; v++)
+    qsort(A->nbr + A->off[v], (size_t)(A->off[v + 1] - A->off[v]), sizeof(int32_t), by_label_then_id);
   return 0;
 }
 
@@ -200,20 +232,23 @@ static void extend(srch *S, int32_t t) {
   }
   int32_t u = S->order[t];
   const adj *A = S->view;
-  /* every valid image of u is a view-neighbour of the image of each assigned
-   * query neighbour of u; scan the shortest of those neighbour lists */
-  int32_t x = S->phi[S->anchor[t]];
+  /* every valid image of u carries u's label and is a view-neighbour of the
+   * image of each assigned query neighbour of u; scan the shortest of those
+   * neighbours' runs of u's label */
+  int64_t lo = 0, hi = 0;
+  label_run(A, S->phi[S->anchor[t]], S->qlab[u], &lo, &hi);
   for (int32_t e = 0; e < S->eq; e++) {
     int32_t a = S->qs[e], b = S->qd[e], w;
     if (a == u) w = b; else if (b == u) w = a; else continue;
     if (!S->used_q[w]) continue;
-    int32_t y = S->phi[w];
-    if (A->off[y + 1] - A->off[y] < A->off[x + 1] - A->off[x]) x = y;
+    int64_t l2, h2;
+    label_run(A, S->phi[w], S->qlab[u], &l2, &h2);
+    if (h2 - l2 < hi - lo) { lo = l2; hi = h2; }
   }
-  for (int64_t p = A->off[x]; p < A->off[x + 1]; p++) {
+  for (int64_t p = lo; p < hi; p++) {
     /* parts: the first searched position's candidates are dealt round-robin by
-     * their place in the anchor's list, so the parts partition the matches */
-    if (t == 2 && S->nshards > 1 && (p - A->off[x]) % S->nshards != S->shard) continue;
+     * their place in the scanned run, so the parts partition the matches */
+    if (t == 2 && S->nshards > 1 && (p - lo) % S->nshards != S->shard) continue;
     int32_t c = A->nbr[p];
     if (++S->nodes > S->budget && S->budget) { S->over_budget = 1; return; }
     if (S->lab[c] != S->qlab[u]) continue;
@@ -348,7 +383,8 @@ int oracle_session_open(int32_t n, const int32_t *labels, int64_t m, const int32
   }
   for (int64_t k = 0; k < b; k++)
     if (op[k] == 1) { ps[mp] = usrc[k]; pd[mp] = udst[k]; mp++; }
-  int rc = (adj_build(&z->AG, n, mu, gs, gd) || adj_build(&z->AP, n, mp, ps, pd)) ? OR_ENOMEM : OR_OK;
+  int rc = (adj_build(&z->AG, n, mu, gs, gd, z->labels) || adj_build(&z->AP, n, mp, ps, pd, z->labels)) ? OR_ENOMEM
+                                                                                                      : OR_OK;
   free(ps); free(pd); free(gs); free(gd);
   if (rc) { oracle_session_close(z); return rc; }
   *out = z;

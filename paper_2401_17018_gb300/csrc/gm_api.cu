@@ -64,6 +64,7 @@ struct gamma_ctx {
   int wpb = 8, tile = 64, grain = 64;
   uint64_t idle_ns = 60ull * 1000000000ull;  // bounded waits of the DFS kernel's work donation
   uint64_t handoff_ns = 1000000000ull;
+  int hub_min = GM_HUB_MIN;  // list length that gets a hash index at load
   int num_sms = 0;
   std::string err;
 
@@ -739,6 +740,7 @@ int gamma_create(const gamma_options *options, gamma_ctx **out) {
   if (o.steal_grain > 0) ctx->grain = o.steal_grain;
   if (o.idle_limit_us) ctx->idle_ns = 1000ull * o.idle_limit_us;
   if (o.handoff_limit_us) ctx->handoff_ns = 1000ull * o.handoff_limit_us;
+  if (o.hub_min_degree > 0) ctx->hub_min = o.hub_min_degree;
   if (ctx->tile < 32 || ctx->tile > 4096 || ctx->wpb > 16) { delete ctx; return GAMMA_EINVAL; }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, o.device);
   if (o.cuda_stream) {
@@ -849,6 +851,8 @@ int gamma_set_options(gamma_ctx *ctx, const gamma_options *o) {
   if (o->steal_grain) ctx->grain = o->steal_grain;
   if (o->idle_limit_us) ctx->idle_ns = 1000ull * o->idle_limit_us;
   if (o->handoff_limit_us) ctx->handoff_ns = 1000ull * o->handoff_limit_us;
+  if (o->hub_min_degree < 0) return ctx->fail(GAMMA_EINVAL, "hub_min_degree must be >= 0");
+  if (o->hub_min_degree > 0) ctx->hub_min = o->hub_min_degree;
   ctx->plan_key.clear();
   return GAMMA_OK;
 }
@@ -947,7 +951,7 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
     uint64_t slots = 0;
     int32_t nh = 0;
     for (int32_t v = 0; v < n; v++) {
-      if (hadj[v].y >= GM_HUB_MIN) {
+      if (hadj[v].y >= (uint32_t)ctx->hub_min) {
         hid[v] = nh++;
         uint64_t c = 8;
         while (c < 3ull * hadj[v].y + 8) c <<= 1;

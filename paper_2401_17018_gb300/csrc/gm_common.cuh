@@ -16,7 +16,7 @@
 #include "../../include/gamma.h"
 
 #define GM_MAXQ 16
-#define GM_HUB_MIN 128          // list length that makes a vertex a hub at load
+#define GM_HUB_MIN 128          // default list length that makes a vertex a hub at load
 #define GM_EMPTY 0x80000000u    // empty hash slot (keys use at most 31 bits when hashing is on)
 #define GM_FULL 0xffffffffu
 #define GM_MAX_DEVICES 128       // device ordinals the library keeps per-device state for
@@ -62,7 +62,7 @@ struct GraphDev {
   uint32_t *etag;        // [pool] batch tag of flagged entries
   uint8_t *nlf;          // [n * nlfw] per-label neighbour counts of the union graph, saturated at 255
   int32_t *vgroup;       // [n] while a batch is staged: the vertex's group in the sorted batch, else -1
-  // hub index: vertices whose list had >= GM_HUB_MIN entries at load keep the
+  // hub index: vertices whose list had >= the hub threshold entries at load keep the
   // start of every label segment and an open-addressing hash set of their keys
   const int32_t *hub_id; // [n] hub number or -1
   uint32_t *hub_lofs;    // [nhub * (nlab + 1)] label-segment starts within the list

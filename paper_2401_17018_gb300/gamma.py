@@ -30,7 +30,8 @@ class gamma_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("flags", ctypes.c_uint32),
                 ("work_budget", ctypes.c_uint64), ("warps_per_block", ctypes.c_int),
                 ("frontier_tile", ctypes.c_int), ("steal_grain", ctypes.c_int),
-                ("idle_limit_us", ctypes.c_uint32), ("handoff_limit_us", ctypes.c_uint32)]
+                ("idle_limit_us", ctypes.c_uint32), ("handoff_limit_us", ctypes.c_uint32),
+                ("hub_min_degree", ctypes.c_int32)]
 
 
 class gamma_matches(ctypes.Structure):
@@ -320,12 +321,12 @@ def gamma_last_error(ctx: int) -> str:
 # ----------------------------------------------------------- convenience
 def make_options(device: int = 0, stream=None, flags: int = 0, work_budget: int = 0, warps_per_block: int = 0,
                  frontier_tile: int = 0, steal_grain: int = 0, idle_limit_us: int = 0,
-                 handoff_limit_us: int = 0) -> gamma_options:
+                 handoff_limit_us: int = 0, hub_min_degree: int = 0) -> gamma_options:
     s = stream
     if s is not None and hasattr(s, "cuda_stream"):
         s = s.cuda_stream
     return gamma_options(device, s, flags, work_budget, warps_per_block, frontier_tile, steal_grain, idle_limit_us,
-                         handoff_limit_us)
+                         handoff_limit_us, hub_min_degree)
 
 
 class Context:
@@ -333,9 +334,9 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None, flags: int = 0, work_budget: int = 0,
                  warps_per_block: int = 0, frontier_tile: int = 0, steal_grain: int = 0, idle_limit_us: int = 0,
-                 handoff_limit_us: int = 0):
+                 handoff_limit_us: int = 0, hub_min_degree: int = 0):
         self._opts = make_options(device, stream, flags, work_budget, warps_per_block, frontier_tile, steal_grain,
-                                  idle_limit_us, handoff_limit_us)
+                                  idle_limit_us, handoff_limit_us, hub_min_degree)
         self.h = gamma_create(self._opts)
         self.b = 0
         self.qsizes = {}
