@@ -263,24 +263,29 @@ static void extend(srch *S, int32_t t) {
   }
 }
 
-/* order for a seeded query edge (a, b): repeatedly take the smallest-id
- * unassigned vertex that has an assigned neighbour; anchor = that neighbour
- * with the smallest id.  Returns 0 if Q is disconnected. */
+/* order for a seeded query edge (a, b): repeatedly take the unassigned
+ * vertex with the most assigned neighbours (ties: the smaller id); anchor =
+ * its assigned neighbour with the smallest id.  Any order in which every
+ * vertex has an assigned neighbour enumerates the same embeddings; this one
+ * checks as many query edges as early as possible.  Returns 0 if Q is
+ * disconnected. */
 static int make_order(srch *S, int32_t a, int32_t b) {
   uint8_t in[32] = {0};
   in[a] = in[b] = 1;
   S->order[0] = a; S->order[1] = b;
   for (int32_t t = 2; t < S->q; t++) {
-    int32_t pick = -1, anc = -1;
-    for (int32_t u = 0; u < S->q && pick < 0; u++) {
+    int32_t pick = -1, anc = -1, best = 0;
+    for (int32_t u = 0; u < S->q; u++) {
       if (in[u]) continue;
+      int32_t nb = 0, first = -1;
       for (int32_t w = 0; w < S->q; w++) {
         if (!in[w]) continue;
         int adjq = 0;
         for (int32_t e = 0; e < S->eq; e++)
           if ((S->qs[e] == u && S->qd[e] == w) || (S->qs[e] == w && S->qd[e] == u)) { adjq = 1; break; }
-        if (adjq) { pick = u; anc = w; break; }
+        if (adjq) { nb++; if (first < 0) first = w; }
       }
+      if (nb > best) { best = nb; pick = u; anc = first; }
     }
     if (pick < 0) return 0;
     in[pick] = 1; S->order[t] = pick; S->anchor[t] = anc;
