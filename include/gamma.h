@@ -159,10 +159,13 @@ GAMMA_API int gamma_apply_batch(gamma_ctx *ctx, int64_t b, const int8_t *op,
  * host array of nreq + 1 offsets).  The result is the same as applying the
  * requests one after another (apply + commit each): request r sees the graph
  * after requests 0..r-1, and its counts, out_pos[r*nq + j] / out_neg[r*nq + j]
- * for query qids[j], are its own incremental matches.  The requests must touch
- * pairwise disjoint edges (else GAMMA_EINVAL, graph unchanged).  Afterwards
- * the batch is staged as with gamma_apply_batch; gamma_commit applies all of
- * it.  No match rows. */
+ * for query qids[j], are its own incremental matches.  Requests may touch the
+ * same edges (a later request may delete an edge an earlier one inserted, or
+ * insert one it deleted); each request must be valid on the graph the earlier
+ * ones leave and touch an edge at most once, else GAMMA_EINVAL with the
+ * smallest offending update index and the graph unchanged.  Afterwards the
+ * batch is staged as with gamma_apply_batch; gamma_commit applies all of it.
+ * No match rows. */
 GAMMA_API int gamma_apply_batches(gamma_ctx *ctx, int32_t nreq, const int64_t *req_off, const int8_t *op,
                                   const int32_t *src, const int32_t *dst, int32_t nq, const int32_t *qids,
                                   uint64_t *out_pos, uint64_t *out_neg);
@@ -295,9 +298,9 @@ GAMMA_API int gamma_recount_noalloc(gamma_ctx *ctx, int32_t cap, uint64_t *out_p
  * GPU is busy wait; when it is free the worker stages every waiting request
  * it can admit together (gamma_apply_batches: continuous batching, each
  * request still gets exactly its own result) and commits them.  A group
- * stops at the first request that touches an edge already in the group, at
- * max_requests / max_updates, or when its estimated device memory would
- * exceed hbm_fraction of the free HBM (admission).  A group that contains an
+ * stops at max_requests / max_updates, or when its estimated device memory
+ * (staging buffers, work items and adjacency growth per update) would exceed
+ * hbm_fraction of the free HBM (admission).  A group that contains an
  * invalid request is served again one request at a time, so only the invalid
  * request fails (GAMMA_EINVAL) and the others get their one-at-a-time
  * results.  While a server runs, its context belongs to the worker thread:

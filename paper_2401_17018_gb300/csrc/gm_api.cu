@@ -379,7 +379,7 @@ int prepare_buffers(gamma_ctx *ctx, int64_t b) {
   if (b > sb.cap) {
     int64_t c = std::max<int64_t>(b, 1024);
     void *ps[] = {sb.cu, sb.cv, sb.cop, sb.keys, sb.tk, sb.vals, sb.tv, sb.head, sb.gid, sb.gv, sb.gstart,
-                  sb.gins, sb.greloc, sb.bkeys};
+                  sb.gins, sb.greloc, sb.bkeys, sb.cnext, sb.cinfo};
     for (void *p : ps) if (p) cudaFree(p);
     sb = StageBufs();
     CKC(cudaMalloc((void **)&sb.cu, 4 * c)); CKC(cudaMalloc((void **)&sb.cv, 4 * c));
@@ -390,6 +390,8 @@ int prepare_buffers(gamma_ctx *ctx, int64_t b) {
     CKC(cudaMalloc((void **)&sb.gv, 8 * c)); CKC(cudaMalloc((void **)&sb.gstart, 8 * c));
     CKC(cudaMalloc((void **)&sb.gins, 8 * c)); CKC(cudaMalloc((void **)&sb.greloc, 8 * c));
     CKC(cudaMalloc((void **)&sb.bkeys, 8 * c));
+    CKC(cudaMalloc((void **)&sb.cnext, 4 * c));
+    CKC(cudaMalloc((void **)&sb.cinfo, c));
     sb.cap = c;
   }
   if (b > ctx->in_cap) {
@@ -425,7 +427,8 @@ int enqueue_stage(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const 
   cudaStream_t s = ctx->stream;
   CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st_init, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
   CKC(cudaEventRecord(ctx->ev[0], s));
-  if (ctx->b > 0) CK(gm_stage(ctx->gd(), dop, dsrc, ddst, ctx->b, ctx->sb, ctx->d_st, s));
+  if (ctx->b > 0)
+    CK(gm_stage(ctx->gd(), dop, dsrc, ddst, ctx->b, ctx->nreq > 1 ? ctx->d_req : nullptr, ctx->sb, ctx->d_st, s));
   CKC(cudaEventRecord(ctx->ev[1], s));
   return GAMMA_OK;
 }
@@ -454,6 +457,7 @@ int enqueue_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_s
   a.items = ctx->d_items; a.item_cap = (uint64_t)ctx->items_cap;
   a.cnt = ctx->d_cnt;
   a.req = (ctx->nreq > 1) ? ctx->d_req : nullptr;
+  a.cnext = (ctx->nreq > 1) ? ctx->sb.cnext : nullptr;
   a.nq = std::max(nq, 1);
   a.per_upd = (ctx->flags & GAMMA_F_PER_UPDATE) ? ctx->d_per_upd : nullptr;
   a.use_filter = (ctx->flags & GAMMA_F_NO_FILTER) ? 0 : 1;
@@ -767,7 +771,7 @@ void gamma_destroy(gamma_ctx *ctx) {
   free_graph(ctx);
   StageBufs &sb = ctx->sb;
   void *ps[] = {sb.cu, sb.cv, sb.cop, sb.keys, sb.tk, sb.vals, sb.tv, sb.head, sb.gid, sb.gv, sb.gstart,
-                sb.gins, sb.greloc, sb.bkeys, ctx->d_in_op, ctx->d_in_src, ctx->d_in_dst, ctx->d_plans,
+                sb.gins, sb.greloc, sb.bkeys, sb.cnext, sb.cinfo, ctx->d_in_op, ctx->d_in_src, ctx->d_in_dst, ctx->d_plans,
                 ctx->d_pair_off, ctx->d_pair_plans, ctx->d_items, ctx->d_cnt, ctx->d_per_upd, ctx->d_rows,
                 ctx->d_tasks, ctx->d_task_seq, ctx->d_sched, ctx->d_req, ctx->d_st};
   for (void *p : ps) if (p) cudaFree(p);
@@ -810,6 +814,7 @@ int gm_recount_prepare(gamma_ctx *ctx, MatchArgs *a, int *nslots, int *num_sms, 
   m.items = ctx->d_items; m.item_cap = (uint64_t)ctx->items_cap;
   m.cnt = nullptr;
   m.req = (ctx->nreq > 1) ? ctx->d_req : nullptr;
+  m.cnext = (ctx->nreq > 1) ? ctx->sb.cnext : nullptr;
   m.nq = std::max(nq, 1);
   m.per_upd = nullptr;
   m.use_filter = (ctx->flags & GAMMA_F_NO_FILTER) ? 0 : 1;
@@ -1125,7 +1130,7 @@ int gamma_commit(gamma_ctx *ctx) {
   cudaStream_t s = ctx->stream;
   CKC(cudaMemsetAsync(&ctx->d_st->live, 0, sizeof(uint64_t), s));
   CKC(cudaEventRecord(ctx->ev[6], s));
-  if (ctx->b > 0) CK(gm_commit(ctx->gd(), ctx->sb, ctx->b, ctx->d_st, s));
+  if (ctx->b > 0) CK(gm_commit(ctx->gd(), ctx->sb, ctx->b, ctx->nreq > 1, ctx->d_st, s));
   CKC(cudaEventRecord(ctx->ev[7], s));
   CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
   CKC(cudaStreamSynchronize(s));

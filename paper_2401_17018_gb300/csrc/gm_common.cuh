@@ -42,7 +42,7 @@ struct GmStatus {
   uint32_t max_label;     // load: largest vertex label
   uint32_t hub_top;       // hub hash slots allocated
   uint32_t tasks_donated; // tasks the last DFS launch split off
-  uint32_t pad;
+  uint32_t n2_valid;      // staged directed entries (the sorted batch's entries before its unused tail)
 };
 
 // DFS scheduling counters, one per 128-byte line (reset before every DFS launch)

@@ -178,13 +178,99 @@ __global__ void k_hub(GraphDev g, const uint32_t *__restrict__ verts, const uint
   }
 }
 
+// ------------------------------- request chains -----------------------------
+// Several requests staged together may touch the same edge: request r sees
+// the graph the requests before it leave.  The updates of one edge, in index
+// order, form a chain; a valid chain alternates insertion and deletion and
+// holds at most one update per request (its head must also agree with G,
+// which the stage checks like any single update).
+
+// edge key (u << idb | v) of every update, with the first checks of an update
+// on its own; an invalid update gets the key ~0 (it sorts last)
+__global__ void k_chain_keys(const int8_t *__restrict__ op, const int32_t *__restrict__ src,
+                             const int32_t *__restrict__ dst, int64_t b, GraphDev g, uint64_t *__restrict__ keys,
+                             uint32_t *__restrict__ idx, GmStatus *st) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b; k += stride) {
+    const int o = op[k];
+    const int32_t s = src[k], d = dst[k];
+    const bool bad = (o != 1 && o != -1) || s < 0 || s >= g.n || d < 0 || d >= g.n || s == d;
+    if (bad) {
+      gm_set_err(st, GAMMA_EINVAL);
+      gm_bad_index(st, k);
+    }
+    const uint64_t u = (uint64_t)min(s, d), v = (uint64_t)max(s, d);
+    keys[k] = bad ? ~0ull : ((u << g.idb) | v);
+    idx[k] = (uint32_t)k;
+  }
+}
+
+// after the stable sort by edge key: link each update to the next one of the
+// same edge, mark heads, check the chains, and record at each head whether
+// the edge exists once the whole chain is applied
+__global__ void k_chain_link(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ idx, int64_t b,
+                             const int8_t *__restrict__ op, const uint32_t *__restrict__ req,
+                             uint32_t *__restrict__ cnext, uint8_t *__restrict__ cinfo, GmStatus *st) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < b; j += stride) {
+    const uint64_t key = keys[j];
+    const uint32_t k = idx[j];
+    if (key == ~0ull) {  // invalid on its own (already reported)
+      cnext[k] = ~0u;
+      cinfo[k] = GM_CHAIN_HEAD;
+      continue;
+    }
+    const bool has_prev = j > 0 && keys[j - 1] == key;
+    const bool has_next = j + 1 < b && keys[j + 1] == key;
+    cnext[k] = has_next ? idx[j + 1] : ~0u;
+    if (has_prev) {
+      const uint32_t kp = idx[j - 1];
+      if (op[kp] == op[k] || req[kp] == req[k]) {  // not alternating, or one request touches the edge twice
+        gm_set_err(st, GAMMA_EINVAL);
+        gm_bad_index(st, (int64_t)k);
+      }
+      cinfo[k] = 0;
+      continue;
+    }
+    int64_t e = j;
+    while (e + 1 < b && keys[e + 1] == key) e++;  // chains are short: one update per request at most
+    uint8_t info = GM_CHAIN_HEAD;
+    if (e > j) info |= GM_CHAIN_LONG;
+    if (op[idx[e]] > 0) info |= GM_CHAIN_PRESENT;
+    cinfo[k] = info;
+  }
+}
+
+// at commit: a chain's head entry carries the head's tag; turn its deletion
+// bit into "absent after the whole chain" so the commit keeps or drops the
+// edge by the chain's last update
+__global__ void k_chain_final(GraphDev g, const uint32_t *__restrict__ cu, const uint32_t *__restrict__ cv, int64_t b,
+                              const uint8_t *__restrict__ cinfo) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b; k += stride) {
+    const uint8_t info = cinfo[k];
+    if (!(info & GM_CHAIN_LONG)) continue;
+    const uint32_t gone = (info & GM_CHAIN_PRESENT) ? 0u : 1u;
+    for (int side = 0; side < 2; side++) {
+      const uint32_t v = side ? cv[k] : cu[k], w = side ? cu[k] : cv[k];
+      const uint2 a = g.adj[v];
+      const uint32_t k32 = gm_key(g.label[w], w, g.idb);
+      const uint32_t p = lb_coherent(g.col + a.x, a.y, k32);
+      if (p < a.y && (g.col[a.x + p] >> 1) == (k32 >> 1)) g.etag[a.x + p] = (g.etag[a.x + p] & ~1u) | gone;
+    }
+  }
+}
+
 // ------------------------------- stage --------------------------------------
 // sort key: (vertex << 33) | (deletion << 32) | adjacency key with flag set,
 // so a vertex's group lists its insertions (sorted) before its deletions.
+// cinfo (chains of several requests, else null): an update that is not the
+// head of its edge's chain enters no list; its entries get the key ~0
 __global__ void k_stage_prep(const int8_t *__restrict__ op, const int32_t *__restrict__ src,
                              const int32_t *__restrict__ dst, int64_t b, GraphDev g,
                              uint32_t *__restrict__ cu, uint32_t *__restrict__ cv, int8_t *__restrict__ cop,
-                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, GmStatus *st) {
+                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                             const uint8_t *__restrict__ cinfo, GmStatus *st) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b; k += stride) {
     int o = op[k];
@@ -202,6 +288,11 @@ __global__ void k_stage_prep(const int8_t *__restrict__ op, const int32_t *__res
     uint32_t u = (uint32_t)min(s, d), v = (uint32_t)max(s, d);
     uint64_t del = (o < 0) ? 1ull : 0ull;
     cu[k] = u; cv[k] = v; cop[k] = (int8_t)o;
+    if (cinfo && !(cinfo[k] & GM_CHAIN_HEAD)) {
+      keys[2 * k] = keys[2 * k + 1] = ~0ull;
+      vals[2 * k] = vals[2 * k + 1] = 0;
+      continue;
+    }
     keys[2 * k] = ((uint64_t)u << 33) | (del << 32) | gm_key(g.label[v], v, g.idb) | 1u;
     keys[2 * k + 1] = ((uint64_t)v << 33) | (del << 32) | gm_key(g.label[u], u, g.idb) | 1u;
     uint32_t val = ((uint32_t)k << 1) | (uint32_t)del;
@@ -249,6 +340,7 @@ __global__ void k_stage_groups(const uint64_t *__restrict__ keys, int64_t n2, co
     uint64_t key = keys[j];
     if (j == n2 - 1) st->ntouched = gid[j] + head[j];
     if (key == ~0ull) continue;
+    if (j == n2 - 1 || keys[j + 1] == ~0ull) st->n2_valid = (uint32_t)(j + 1);  // unused entries sort last
     uint32_t gi = gid[j] + head[j] - 1;  // gid is the exclusive scan of the head flags
     if (head[j]) { gv[gi] = (uint32_t)(key >> 33); gstart[gi] = (uint32_t)j; }
     if (!((key >> 32) & 1ull)) atomicAdd(&gins[gi], 1u);
@@ -303,7 +395,7 @@ __global__ void k_stage_merge(GraphDev g, const uint64_t *__restrict__ keys, con
   for (int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gi < nt; gi += nw) {
     const uint32_t v = gv[gi];
     const uint32_t start = gstart[gi];
-    const uint32_t end = (gi + 1 < nt) ? gstart[gi + 1] : (uint32_t)n2;
+    const uint32_t end = (gi + 1 < nt) ? gstart[gi + 1] : st->n2_valid;
     const uint32_t ni = gins[gi];
     const uint2 a = g.adj[v];
     const uint32_t na = a.y, tot = na + ni;
@@ -516,13 +608,25 @@ int gm_hub(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32
   return GAMMA_OK;
 }
 
-int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, int64_t b, StageBufs &sb,
-             GmStatus *st, cudaStream_t s) {
+int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, int64_t b, const uint32_t *req,
+             StageBufs &sb, GmStatus *st, cudaStream_t s) {
   const int64_t n2 = 2 * b;
-  k_stage_prep<<<grid_for(b, 256), 256, 0, s>>>(op, src, dst, b, g, sb.cu, sb.cv, sb.cop, sb.keys, sb.vals, st);
+  int rc = GAMMA_OK;
+  if (req) {  // chains of updates on one edge across requests (the sort buffers serve as scratch)
+    k_chain_keys<<<grid_for(b, 256), 256, 0, s>>>(op, src, dst, b, g, sb.keys, sb.vals, st);
+    GM_LAUNCHED();
+    GM_CUDA(cudaGetLastError());
+    rc = gm_radix_sort(sb.keys, sb.vals, sb.tk, sb.tv, b, 0, 2 * g.idb, s);
+    if (rc) return rc;
+    k_chain_link<<<grid_for(b, 256), 256, 0, s>>>(sb.keys, sb.vals, b, op, req, sb.cnext, sb.cinfo, st);
+    GM_LAUNCHED();
+    GM_CUDA(cudaGetLastError());
+  }
+  k_stage_prep<<<grid_for(b, 256), 256, 0, s>>>(op, src, dst, b, g, sb.cu, sb.cv, sb.cop, sb.keys, sb.vals,
+                                                req ? sb.cinfo : nullptr, st);
   GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
-  int rc = gm_radix_sort(sb.keys, sb.vals, sb.tk, sb.tv, n2, 1, 33 + g.idb, s);
+  rc = gm_radix_sort(sb.keys, sb.vals, sb.tk, sb.tv, n2, 1, 33 + g.idb, s);
   if (rc) return rc;
   k_stage_check<<<grid_for(n2, 256), 256, 0, s>>>(sb.keys, sb.vals, n2, g, sb.head, st);
   GM_LAUNCHED();
@@ -550,8 +654,13 @@ int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *ds
   return gm_hub(g, sb.gv, &st->ntouched, (uint32_t)n2, st, s);
 }
 
-int gm_commit(GraphDev g, const StageBufs &sb, int64_t b, GmStatus *st, cudaStream_t s) {
+int gm_commit(GraphDev g, const StageBufs &sb, int64_t b, bool chains, GmStatus *st, cudaStream_t s) {
   const int64_t n2 = 2 * b;
+  if (chains) {
+    k_chain_final<<<grid_for(b, 256), 256, 0, s>>>(g, sb.cu, sb.cv, b, sb.cinfo);
+    GM_LAUNCHED();
+    GM_CUDA(cudaGetLastError());
+  }
   int64_t mb = (n2 * 32 + 255) / 256;
   if (mb > 16384) mb = 16384;
   if (mb < 1) mb = 1;

@@ -12,8 +12,15 @@ struct StageBufs {
   uint32_t *head = nullptr, *gid = nullptr;
   uint32_t *gv = nullptr, *gstart = nullptr, *gins = nullptr, *greloc = nullptr;
   uint32_t *bkeys = nullptr;
+  // several requests staged together: the updates of one edge form a chain
+  // in index order; only its first update (the head) enters the adjacency
+  uint32_t *cnext = nullptr;  // [b] next update of the same edge, or ~0
+  uint8_t *cinfo = nullptr;   // [b] GM_CHAIN_* bits
   int64_t cap = 0;  // updates
 };
+#define GM_CHAIN_HEAD 1u      // the update is the first of its edge's chain
+#define GM_CHAIN_LONG 2u      // (head) later updates of the same edge follow
+#define GM_CHAIN_PRESENT 4u   // (head) the edge exists once the whole chain is applied
 
 int gm_load_validate(const int32_t *labels, int32_t n, const int32_t *src, const int32_t *dst, int64_t m,
                      GmStatus *st, cudaStream_t s);
@@ -23,9 +30,12 @@ int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m,
 int gm_nlf(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32_t nverts_max, cudaStream_t s);
 int gm_hub(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32_t nverts_max, GmStatus *st,
            cudaStream_t s);
-int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, int64_t b, StageBufs &sb,
-             GmStatus *st, cudaStream_t s);
-int gm_commit(GraphDev g, const StageBufs &sb, int64_t b, GmStatus *st, cudaStream_t s);
+// req: [b] request of each update when several requests are staged together
+// (null: one request); then updates of different requests may touch the same
+// edge, each request valid on the graph the earlier ones leave
+int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, int64_t b, const uint32_t *req,
+             StageBufs &sb, GmStatus *st, cudaStream_t s);
+int gm_commit(GraphDev g, const StageBufs &sb, int64_t b, bool chains, GmStatus *st, cudaStream_t s);
 // per-query form: the next DFS launch starts at the items the next seed launch appends
 int gm_begin_group(GmStatus *st, cudaStream_t s);
 
@@ -44,6 +54,7 @@ struct MatchArgs {
   uint64_t item_cap;
   uint64_t *cnt;               // [nreq * nq * 2] positive / negative counts
   const uint32_t *req;         // [b] request of each update (null: one request)
+  const uint32_t *cnext;       // [b] next update of the same edge (with req), else null
   int nq;                      // query slots per request
   uint64_t *per_upd;           // [nq * b] or null
   int use_filter;

@@ -40,17 +40,26 @@ __device__ __forceinline__ int warp_read(const int32_t *p) {
 // seed of update `upd` with sign `sdel` from request `r`.  Same request: the
 // seed's view (G' for insertions, G for deletions) plus the charging rule
 // (only same-sign updates of larger index).  Several requests staged together
-// are applied in order: an earlier request's insertion is already present and
-// its deletion already gone; a later request's insertion is not there yet and
-// its deletion has not happened yet.
+// are applied in order: the tag is the first update of the edge's chain, the
+// later ones follow through cnext; an earlier request's insertion is already
+// present and its deletion already gone, a later request's update has not
+// happened yet (so the edge is there exactly when the chain's first update is
+// a deletion, or the last earlier request inserted it).
 __device__ __forceinline__ bool tag_ok(uint32_t t, uint32_t sdel, uint32_t upd, const uint32_t *req,
-                                       uint32_t r) {
-  const uint32_t k = t >> 1, d = t & 1u;
-  if (req) {
+                                       uint32_t r, const uint32_t *cnext, const int8_t *op) {
+  uint32_t k = t >> 1, d = t & 1u;
+  if (!req) return d == sdel && k > upd;
+  bool present = d == 1u;  // before the chain's first update
+  while (true) {
     const uint32_t rk = __ldg(req + k);
-    if (rk != r) return (rk < r) ? (d == 0u) : (d == 1u);
+    if (rk == r) return d == sdel && k > upd;
+    if (rk > r) return present;
+    present = d == 0u;  // after an earlier request's update
+    const uint32_t nx = cnext ? __ldg(cnext + k) : ~0u;
+    if (nx == ~0u) return present;
+    k = nx;
+    d = __ldg(op + k) < 0 ? 1u : 0u;
   }
-  return d == sdel && k > upd;
 }
 
 // is the edge (w, c) visible in the seed's view under the charging rule?
@@ -74,7 +83,8 @@ __device__ __forceinline__ uint32_t probe_bytes(uint32_t d) {
 
 template <bool C>
 __device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t x, uint32_t sdel,
-                                        uint32_t upd, const uint32_t *req, uint32_t r, ByteCount<C> &bytes) {
+                                        uint32_t upd, const uint32_t *req, uint32_t r, const uint32_t *cnext,
+                                        const int8_t *op, ByteCount<C> &bytes) {
   const uint32_t key = x & ~1u;
   const int32_t h = __ldg(g.hub_id + w);
   if (h >= 0) {
@@ -104,7 +114,7 @@ __device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t 
   if (p >= a.y) return false;
   uint32_t y = __ldg(L + p);
   if ((y | 1u) != (key | 1u)) return false;
-  if (y & 1u) return tag_ok(__ldg(g.etag + a.x + p), sdel, upd, req, r);
+  if (y & 1u) return tag_ok(__ldg(g.etag + a.x + p), sdel, upd, req, r, cnext, op);
   return true;
 }
 
@@ -663,7 +673,7 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
                 const uint32_t kj = (uint32_t)__ldg(a.bkeys + j) & ~1u;
                 lbytes += 12;
                 if (kj > k_hi) break;
-                if (!tag_ok(__ldg(a.bvals + j), sdel, upd, a.req, rq)) cntv--;
+                if (!tag_ok(__ldg(a.bvals + j), sdel, upd, a.req, rq, a.cnext, a.op)) cntv--;
               }
             }
           }
@@ -673,7 +683,7 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
         auto conflict = [&](uint32_t v, uint32_t mv, uint32_t k_lo, uint32_t k_hi) -> uint32_t {
           const uint32_t kj = gm_key(lab, mv, g.idb);
           if (kj < k_lo || kj > k_hi) return 0u;
-          return edge_ok(g, v, kj, sdel, upd, a.req, rq, lbytes) ? 1u : 0u;
+          return edge_ok(g, v, kj, sdel, upd, a.req, rq, a.cnext, a.op, lbytes) ? 1u : 0u;
         };
         if (lev < 0) {
           if (lane == 0) {
@@ -761,7 +771,7 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       chunks++;
       uint32_t x = ok ? __ldg(g.col + slot2) : 0u;
       const uint32_t id = (x >> 1) & g.idmask;
-      if (ok && (x & 1u)) ok = tag_ok(__ldg(g.etag + slot2), sdel, upd, a.req, rq);
+      if (ok && (x & 1u)) ok = tag_ok(__ldg(g.etag + slot2), sdel, upd, a.req, rq, a.cnext, a.op);
       const uint16_t chk_edge = P.bwd[c] & (uint16_t)~(1u << drv);
       const uint16_t chk_neq = P.samelab[c];
       if (ok && (chk_edge | chk_neq)) {
@@ -773,13 +783,13 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
           const int pos = l2 + 2;
           const uint32_t vv = V[l2 * T + ee];
           if ((chk_neq >> pos) & 1) ok = (vv != id);
-          if (ok && ((chk_edge >> pos) & 1)) ok = edge_ok(g, vv, x, sdel, upd, a.req, rq, lbytes);
+          if (ok && ((chk_edge >> pos) & 1)) ok = edge_ok(g, vv, x, sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
           ee = PAR[l2 * T + ee];
         }
         if (ok && ((chk_neq >> 1) & 1)) ok = (m1 != id);
-        if (ok && ((chk_edge >> 1) & 1)) ok = edge_ok(g, m1, x, sdel, upd, a.req, rq, lbytes);
+        if (ok && ((chk_edge >> 1) & 1)) ok = edge_ok(g, m1, x, sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
         if (ok && (chk_neq & 1)) ok = (m0 != id);
-        if (ok && (chk_edge & 1)) ok = edge_ok(g, m0, x, sdel, upd, a.req, rq, lbytes);
+        if (ok && (chk_edge & 1)) ok = edge_ok(g, m0, x, sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
       }
       if (ok && stored && a.use_filter) ok = nlf_ok(g, id, P, c);
       if (gidx < total) lbytes += ((x & 1u) ? 8u : 4u) + (ok ? 8u : 0u);

@@ -3,14 +3,14 @@
 //
 // Continuous batching: requests that arrive while a group is on the GPU wait
 // in a FIFO; when the GPU is free, the worker takes every waiting request it
-// can admit -- in order, until one would touch an edge already in the group,
-// or the group would exceed the update / request caps, or its estimated
-// device memory would exceed a fraction of the free HBM -- and stages them
-// together with gamma_apply_batches, so their seeding and DFS run in the same
-// launches while each request still gets exactly the result it would get on
-// its own (request r sees the graph after requests 0..r-1).  The group is then
-// committed.  A request is copied into pinned host memory by the submitting
-// thread, which overlaps with the GPU work of the current group.
+// can admit -- in order, until the group would exceed the update / request
+// caps or its estimated device memory would exceed a fraction of the free
+// HBM -- and stages them together with gamma_apply_batches, so their seeding
+// and DFS run in the same launches while each request still gets exactly the
+// result it would get on its own (request r sees the graph after requests
+// 0..r-1; requests may touch the same edges).  The group is then committed.
+// A request is copied into pinned host memory by the submitting thread, which
+// overlaps with the GPU work of the current group.
 #include <string.h>
 
 #include <chrono>
@@ -19,7 +19,6 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
-#include <unordered_set>
 #include <vector>
 
 #include "gm_common.cuh"
@@ -40,11 +39,6 @@ struct Request {
 
 double now_ms(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-}
-
-uint64_t edge_key(int32_t a, int32_t b) {
-  uint32_t lo = (uint32_t)(a < b ? a : b), hi = (uint32_t)(a < b ? b : a);
-  return ((uint64_t)lo << 32) | hi;
 }
 
 void free_request(Request *r) {
@@ -91,13 +85,21 @@ struct gamma_server {
   }
 
   // device bytes a group of n updates may need beyond the resident graph:
-  // staging (keys, values, groups, sort buffers) and work items
-  static uint64_t est_bytes(int64_t n) { return (uint64_t)n * 256ull + (64ull << 20); }
+  // the staging buffers (inputs 9 B, canonical endpoints and op 9 B, sort keys
+  // and values with their alternates 48 B, vertex groups 32 B, sorted batch
+  // keys 8 B, request and chain links 9 B per update), the DFS work items
+  // (up to 8 per update at 16 B) and the adjacency pool's growth when touched
+  // lists outgrow their slack (a moved list takes 1.25x its entries; about 2
+  // entries of 4 B per update on average, counted at 4x for skewed lists),
+  // plus the fixed task ring, counts and status (64 MiB)
+  static uint64_t est_bytes(int64_t n) {
+    const uint64_t per_update = 9 + 9 + 48 + 32 + 8 + 9 + 8 * 16 + 4 * 2 * 4;
+    return (uint64_t)n * per_update + (64ull << 20);
+  }
 
   void run() {
     cudaSetDevice(ctx_device());
     std::vector<Request *> group;
-    std::unordered_set<uint64_t> edges;
     for (;;) {
       group.clear();
       {
@@ -108,17 +110,12 @@ struct gamma_server {
         cudaMemGetInfo(&free_b, &total_b);
         const double budget = opt.hbm_fraction * (double)free_b;
         int64_t nupd = 0;
-        edges.clear();
         while (!pending.empty()) {
           Request *r = pending.front();
           if (!group.empty()) {
             if ((int)group.size() >= opt.max_requests || nupd + r->b > opt.max_updates) break;
             if ((double)est_bytes(nupd + r->b) > budget) break;
-            bool clash = false;
-            for (int64_t k = 0; k < r->b && !clash; k++) clash = edges.count(edge_key(r->src[k], r->dst[k])) != 0;
-            if (clash) break;
           }
-          for (int64_t k = 0; k < r->b; k++) edges.insert(edge_key(r->src[k], r->dst[k]));
           nupd += r->b;
           group.push_back(r);
           pending.pop_front();

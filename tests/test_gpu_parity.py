@@ -433,18 +433,78 @@ def test_requests_alone_equal_in_the_mix(G, flags):
         cs, cd = I.apply_batch_edges(cs, cd, rb)
 
 
-def test_requests_touching_the_same_edge_are_rejected(G):
+@pytest.mark.parametrize("flags", [0, 8])
+def test_requests_sharing_edges_equal_one_at_a_time(G, flags):
+    """Requests staged together may touch the same edges: the served stream's
+    generator deletes edges earlier requests inserted and re-inserts deleted
+    ones.  Each request gets its one-at-a-time counts (checked against the
+    oracle on the graph the earlier requests leave) and the committed graph
+    equals the one-at-a-time graph."""
     w = I.make_workload("tiny")
-    e = (int(w.pool_src[0]), int(w.pool_dst[0]))
-    op = np.array([1, -1], np.int8)
-    src = np.array([e[0], e[0]], np.int32)
-    dst = np.array([e[1], e[1]], np.int32)
+    reqs = I.served_stream(w, 12, 7, 0.5, 2.2)
+    keys = [set(I.edge_keys(r.src, r.dst).tolist()) for r in reqs]
+    assert any(keys[i] & keys[j] for i in range(len(keys)) for j in range(i))  # the case shares edges
+    qs = [I.TRIANGLE_WITH_TAIL, I.pattern_query([0, 1, 2], [(0, 1), (1, 2)]), I.pattern_query([1, 1], [(0, 1)])]
+    alone = []
+    with G.Context() as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        for r in reqs:
+            pos, neg = ctx.apply_batch(r.op, r.src, r.dst, qids)
+            alone.append((pos.tolist(), neg.tolist()))
+            ctx.commit()
+        after_alone = ctx.export_adjacency(w.graph.n)
+    with G.Context(flags=flags | G.GAMMA_F_PER_UPDATE) as ctx:
+        ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
+        qids = [ctx.register_query(q.labels, q.src, q.dst) for q in qs]
+        off = np.concatenate([[0], np.cumsum([len(r) for r in reqs])])
+        cat = lambda f: np.concatenate([getattr(r, f) for r in reqs])
+        pos, neg = ctx.apply_batches(off, cat("op"), cat("src"), cat("dst"), qids)
+        per = np.stack([ctx.update_counts(j) for j in range(len(qids))])
+        ctx.commit()
+        after_mix = ctx.export_adjacency(w.graph.n)
+    assert [(pos[r].tolist(), neg[r].tolist()) for r in range(len(reqs))] == alone
+    assert np.array_equal(after_alone[0], after_mix[0]) and np.array_equal(after_alone[1], after_mix[1])
+    cs, cd = w.graph.src, w.graph.dst
+    for r, rb in enumerate(reqs):
+        c = O.bdsm_multi(w.graph.n, w.graph.labels, cs, cd, qs, rb)
+        assert np.array_equal(per[:, off[r]:off[r + 1]], c)
+        cs, cd = I.apply_batch_edges(cs, cd, rb)
+
+
+def test_invalid_request_chains_are_rejected(G):
+    """A request must be valid on the graph the earlier requests leave and may
+    touch an edge once: inserting an edge an earlier request inserted, a
+    request touching one edge twice, and deleting an edge no earlier request
+    inserted are rejected with the offending index, the graph unchanged."""
+    w = I.make_workload("tiny")
+    e = (int(w.pool_src[0]), int(w.pool_dst[0]))  # not in G0
+    f = (int(w.pool_src[1]), int(w.pool_dst[1]))
+    cases = [
+        ([0, 1, 2], [1, 1], [e, e], 1),                 # inserted twice, by two requests
+        ([0, 2], [1, -1], [e, e], 1),                   # one request touches the edge twice
+        ([0, 1, 2, 3], [1, -1, -1], [f, e, e], 1),      # deletes an edge that is absent
+        ([0, 1, 2, 3], [1, -1, 1], [e, e, e], None),    # insert, delete, insert: valid
+    ]
     with G.Context() as ctx:
         ctx.load_graph(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst)
         qid = ctx.register_query([0, 1], [0], [1])
-        with pytest.raises(G.GammaError) as ex:
-            ctx.apply_batches(np.array([0, 1, 2]), op, src, dst, [qid])
-        assert ex.value.code == G.GAMMA_EINVAL
+        before = ctx.export_adjacency(w.graph.n)
+        for off, ops, edges, bad in cases:
+            op = np.array(ops, np.int8)
+            src = np.array([x[0] for x in edges], np.int32)
+            dst = np.array([x[1] for x in edges], np.int32)
+            if bad is None:
+                ctx.apply_batches(np.array(off), op, src, dst, [qid])
+                ctx.commit()
+                after = ctx.export_adjacency(w.graph.n)
+                assert after[0][-1] == before[0][-1] + 2  # e is in the graph once
+                continue
+            with pytest.raises(G.GammaError) as ex:
+                ctx.apply_batches(np.array(off), op, src, dst, [qid])
+            assert ex.value.code == G.GAMMA_EINVAL and ("update %d " % bad) in str(ex.value)
+            now = ctx.export_adjacency(w.graph.n)
+            assert np.array_equal(now[0], before[0]) and np.array_equal(now[1], before[1])
 
 
 def test_server_results_equal_sequential(G):
