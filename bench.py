@@ -55,10 +55,12 @@ WORKLOADS = {
     # profiler capture sees the steady state of the full batch
     "mid_20k": {"workload": "mid", "queries": "tests/golden/queries_mid.json", "n_ins": 90_000, "n_del": 10_000,
                 "first": 20000},
-    # the large graph and queries with the first 20,000 updates of its first
-    # batch: a profiling case for the kernel on the large graph
+    # the large graph and queries with the first 20,000 / 100,000 updates of
+    # its first batch: profiling cases for the kernel on the large graph
     "large_20k": {"workload": "large", "queries": "tests/golden/queries_large.json", "n_ins": 800_000,
                   "n_del": 200_000, "batches": 1, "first": 20000},
+    "large_100k": {"workload": "large", "queries": "tests/golden/queries_large.json", "n_ins": 800_000,
+                   "n_del": 200_000, "batches": 1, "first": 100000},
     "tiny": {"workload": "tiny", "queries": None, "n_ins": 256, "n_del": 0},
 }
 DESCRIBE = {
@@ -66,6 +68,8 @@ DESCRIBE = {
              "batches of 1,000,000 updates (800,000 ins + 200,000 del) with a commit after each, one batch per step",
     "large_20k": "R-MAT scale 23, 60.4M edges, 16 labels Zipf(1.0), %d queries of %s vertices, the first 20,000 "
                  "updates of the first large batch, batch and inverse alternating",
+    "large_100k": "R-MAT scale 23, 60.4M edges, 16 labels Zipf(1.0), %d queries of %s vertices, the first 100,000 "
+                  "updates of the first large batch, batch and inverse alternating",
     "mid": "R-MAT scale 20, 7.55M edges, 8 labels Zipf(1.2), %d queries of %s vertices, batch of 100,000 updates "
            "(90,000 ins + 10,000 del), batch and inverse alternating",
     "mid_3k": "R-MAT scale 20, 7.55M edges, 8 labels Zipf(1.2), %d queries of %s vertices, the first 3,000 updates "
@@ -509,7 +513,7 @@ def main():
     ap.add_argument("--full-grid", action="store_true", help="batched mode: sweep the whole autotuner grid")
     ap.add_argument("--first", type=int, default=0,
                     help="batched mode: keep only the first N updates of the batch (0 = all)")
-    ap.add_argument("--batches", type=int, default=12, help="served mode: batches in the stream")
+    ap.add_argument("--batches", type=int, default=2000, help="served mode: batches in the stream")
     ap.add_argument("--size-exp", type=float, nargs=2, default=[3.0, 6.0],
                     help="served mode: batch sizes floor(10^U(a, b))")
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 0.95],

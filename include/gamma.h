@@ -60,6 +60,9 @@ extern "C" {
 #define GAMMA_F_COUNT_BYTES 0x10u /* count the DFS kernel's algorithmic bytes (gamma_stats.alg_bytes) */
 #define GAMMA_F_NO_LEAF 0x20u   /* always enumerate a last query vertex that has one earlier neighbour
                                    (default: count it in closed form when no rows are requested) */
+#define GAMMA_F_NO_SHARE 0x40u  /* expand every partial match at the last query vertex (default: when that
+                                   vertex is not adjacent to the one before it and no rows are requested,
+                                   the children of one partial match share their candidates) */
 
 typedef struct gamma_ctx gamma_ctx;
 

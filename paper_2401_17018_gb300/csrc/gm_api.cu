@@ -346,7 +346,7 @@ int grow_pool(gamma_ctx *ctx, uint64_t need) {
   if (cap >= (1ull << 32) - 64) cap = (1ull << 32) - 64;
   if (cap <= ctx->pool_cap) return ctx->fail(GAMMA_ENOMEM, "adjacency pool cannot grow past 2^32 slots");
   uint32_t *col = nullptr, *etag = nullptr;
-  CKC(cudaMalloc((void **)&col, sizeof(uint32_t) * cap));
+  CKC(cudaMalloc((void **)&col, sizeof(uint32_t) * (cap + GM_COL_PAD)));  // padded: short lists are read in 16-byte words
   CKC(cudaMalloc((void **)&etag, sizeof(uint32_t) * cap));
   CKC(cudaMemcpyAsync(col, ctx->d_col, sizeof(uint32_t) * ctx->pool_top, cudaMemcpyDeviceToDevice, ctx->stream));
   CKC(cudaMemcpyAsync(etag, ctx->d_etag, sizeof(uint32_t) * ctx->pool_top, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -467,6 +467,7 @@ int enqueue_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_s
   a.warps_per_block = ctx->wpb;
   a.count_bytes = (ctx->flags & GAMMA_F_COUNT_BYTES) ? 1 : 0;
   a.leaf = (ctx->flags & GAMMA_F_NO_LEAF) ? 0 : 1;
+  a.share = (rows_dev == nullptr && !(ctx->flags & GAMMA_F_NO_SHARE)) ? 1 : 0;
   a.bkeys = ctx->sb.keys;
   a.bvals = ctx->sb.vals;
   a.gstart = ctx->sb.gstart;
@@ -825,6 +826,7 @@ int gm_recount_prepare(gamma_ctx *ctx, MatchArgs *a, int *nslots, int *num_sms, 
   m.warps_per_block = ctx->wpb;
   m.count_bytes = 0;
   m.leaf = (ctx->flags & GAMMA_F_NO_LEAF) ? 0 : 1;
+  m.share = (ctx->flags & GAMMA_F_NO_SHARE) ? 0 : 1;
   m.bkeys = ctx->sb.keys; m.bvals = ctx->sb.vals; m.gstart = ctx->sb.gstart; m.gins = ctx->sb.gins;
   m.n2 = (uint32_t)(2 * ctx->b);
   m.tasks = nullptr; m.sched = nullptr; m.task_seq = nullptr; m.task_cap = 0;
@@ -966,10 +968,12 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
     ctx->nhub = nh;
     CKC(cudaMalloc((void **)&ctx->d_hub_id, sizeof(int32_t) * n));
     CKC(cudaMemcpy(ctx->d_hub_id, hid.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    // hash-table descriptor per vertex (zero: none), so a membership test
+    // reads it with one load instead of going through the hub number
+    CKC(cudaMalloc((void **)&ctx->d_hub_tab, sizeof(uint2) * (size_t)n));
+    CKC(cudaMemset(ctx->d_hub_tab, 0, sizeof(uint2) * (size_t)n));
     if (nh > 0) {
       CKC(cudaMalloc((void **)&ctx->d_hub_lofs, sizeof(uint32_t) * (size_t)nh * (ctx->nlab + 1)));
-      CKC(cudaMalloc((void **)&ctx->d_hub_tab, sizeof(uint2) * (size_t)nh));
-      CKC(cudaMemset(ctx->d_hub_tab, 0, sizeof(uint2) * (size_t)nh));
       // keys need their top bit free for the empty marker
       if (1 + ctx->idb + lb < 32) {
         uint64_t cap = 2 * slots + (1u << 20);
@@ -1363,6 +1367,7 @@ int gamma_add_vertices(gamma_ctx *ctx, int32_t k, const int32_t *labels, int32_t
   CK(grow_vertex_array(ctx, &ctx->d_nlf, (size_t)ctx->nlfw, n, m2, 0));
   CK(grow_vertex_array(ctx, &ctx->d_vgroup, sizeof(int32_t), n, m2, 0xff));
   CK(grow_vertex_array(ctx, &ctx->d_hub_id, sizeof(int32_t), n, m2, 0xff));
+  CK(grow_vertex_array(ctx, &ctx->d_hub_tab, sizeof(uint2), n, m2, 0));
   for (int32_t i = 0; i < k; i++) ctx->label_freq[hl[i]]++;
   ctx->n = m2;
   return GAMMA_OK;

@@ -16,7 +16,9 @@
 #include "../../include/gamma.h"
 
 #define GM_MAXQ 16
-#define GM_HUB_MIN 128          // default list length that makes a vertex a hub at load
+#define GM_HUB_MIN 16           // default list length that makes a vertex a hub (hash-indexed) at load
+#define GM_SCAN_MAX 16          // lists up to this length are read whole for a membership test
+#define GM_COL_PAD 8            // words after the adjacency pool, so 16-byte reads of a short list stay inside
 #define GM_EMPTY 0x80000000u    // empty hash slot (keys use at most 31 bits when hashing is on)
 #define GM_FULL 0xffffffffu
 #define GM_MAX_DEVICES 128       // device ordinals the library keeps per-device state for
@@ -66,7 +68,7 @@ struct GraphDev {
   // start of every label segment and an open-addressing hash set of their keys
   const int32_t *hub_id; // [n] hub number or -1
   uint32_t *hub_lofs;    // [nhub * (nlab + 1)] label-segment starts within the list
-  uint2 *hub_tab;        // [nhub] {first slot in hub_keys, log2 capacity} (capacity 0: no table)
+  uint2 *hub_tab;        // [n] per vertex {first slot in hub_keys, log2 capacity} (capacity 0: no table)
   uint32_t *hub_keys;    // hash slots (GM_EMPTY or an adjacency key)
   uint32_t hub_keys_cap;
   int32_t nhub;

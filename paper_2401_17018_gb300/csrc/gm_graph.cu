@@ -144,7 +144,7 @@ __global__ void k_hub(GraphDev g, const uint32_t *__restrict__ verts, const uint
       if (l <= g.nlab) lofs[l] = (l >= g.nlab) ? a.y : lb_coherent(L, a.y, (uint32_t)l << s);
     }
     if (g.hub_keys == nullptr) continue;
-    uint2 t = g.hub_tab[h];
+    uint2 t = g.hub_tab[v];
     uint32_t cap = t.y ? (1u << t.y) : 0u;
     if (2ull * a.y + 2 > cap) {
       uint32_t bits = 3;
@@ -158,7 +158,7 @@ __global__ void k_hub(GraphDev g, const uint32_t *__restrict__ verts, const uint
       off = __shfl_sync(GM_FULL, off, 0);
       ok = __shfl_sync(GM_FULL, ok, 0);
       t = ok ? make_uint2(off, bits) : make_uint2(0, 0);
-      if (lane == 0) g.hub_tab[h] = t;
+      if (lane == 0) g.hub_tab[v] = t;
       cap = t.y ? (1u << t.y) : 0u;
     }
     if (!cap) continue;
@@ -565,7 +565,7 @@ int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m,
   uint64_t cap = (uint64_t)(used * pool_factor) + pool_reserve + 64;
   if (cap >= (1ull << 32) - 64) return GAMMA_ENOMEM;
   uint32_t *col = nullptr, *etag = nullptr;
-  GM_CUDA(cudaMalloc((void **)&col, sizeof(uint32_t) * cap));
+  GM_CUDA(cudaMalloc((void **)&col, sizeof(uint32_t) * (cap + GM_COL_PAD)));  // padded: short lists are read in 16-byte words
   GM_CUDA(cudaMalloc((void **)&etag, sizeof(uint32_t) * cap));
   if (m > 0) {
     k_load_scatter<<<grid_for(n2, 256), 256, 0, s>>>(keys, n2, flag, pos, rowstart, off, col);

@@ -67,6 +67,7 @@ struct MatchArgs {
   int warps_per_block;
   int count_bytes;             // accumulate algorithmic bytes into st->alg_bytes
   int leaf;                    // count a last position with one backward neighbour in closed form
+  int share;                   // siblings share last-position candidates (counts only)
   const uint64_t *bkeys;       // the staged batch, sorted: (vertex << 33 | deletion << 32 | key)
   const uint32_t *bvals;       // its tags
   const uint32_t *gstart;      // [groups] first sorted entry of each touched vertex

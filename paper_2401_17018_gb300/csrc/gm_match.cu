@@ -62,8 +62,6 @@ __device__ __forceinline__ bool tag_ok(uint32_t t, uint32_t sdel, uint32_t upd, 
   }
 }
 
-// is the edge (w, c) visible in the seed's view under the charging rule?
-// x = adjacency key of c (flag bit ignored)
 // Algorithmic-byte accumulator: counts only in the instrumented build of the
 // DFS kernel (C = true); in the timed build every update compiles away.
 template <bool C>
@@ -81,33 +79,69 @@ __device__ __forceinline__ uint32_t probe_bytes(uint32_t d) {
   return min(4u * d, 32u * steps) + 8u;
 }
 
+// A list's membership index in 8 bytes: {first hash slot, log2 capacity} for
+// a hash-indexed list, else {list offset, length | GM_DESC_LIST}.
+#define GM_DESC_LIST 0x80000000u
+__device__ __forceinline__ uint2 edge_desc(const GraphDev &g, uint32_t w) {
+  const uint2 t = __ldg(g.hub_tab + w);
+  if (t.y) return t;
+  const uint2 a = __ldg(reinterpret_cast<const uint2 *>(g.adj) + w);
+  return make_uint2(a.x, a.y | GM_DESC_LIST);
+}
+
+// is the edge (w, c) visible in the seed's view under the charging rule?
+// x = adjacency key of c (flag bit ignored), D = edge_desc(g, w)
 template <bool C>
-__device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t x, uint32_t sdel,
-                                        uint32_t upd, const uint32_t *req, uint32_t r, const uint32_t *cnext,
-                                        const int8_t *op, ByteCount<C> &bytes) {
+__device__ __forceinline__ bool edge_ok_d(const GraphDev &g, uint32_t w, uint2 D, uint32_t x, uint32_t sdel,
+                                          uint32_t upd, const uint32_t *req, uint32_t r, const uint32_t *cnext,
+                                          const int8_t *op, ByteCount<C> &bytes) {
   const uint32_t key = x & ~1u;
-  const int32_t h = __ldg(g.hub_id + w);
-  if (h >= 0) {
-    // hub: probe its hash set; a flagged key still needs the tag from the list
-    const uint2 t = __ldg(g.hub_tab + h);
-    if (t.y) {
-      const uint32_t mask = (1u << t.y) - 1u;
-      const uint32_t *T = g.hub_keys + t.x;
-      uint32_t p = gm_hash(key >> 1) & mask;
-      bytes += 12;
-      for (uint32_t probe = 0; probe <= mask; probe++) {
-        const uint32_t e = __ldg(T + p);
-        bytes += (probe == 0 || (p & 7u) == 0) ? 32 : 0;
-        if (e == GM_EMPTY) return false;
-        if ((e | 1u) == (key | 1u)) {
-          if (!(e & 1u)) return true;
-          break;  // batch edge: fetch its tag below
+  uint2 a;
+  if (!(D.y & GM_DESC_LIST)) {
+    // hash-indexed list: probe its set; a flagged key still needs the tag from the list
+    const uint32_t mask = (1u << D.y) - 1u;
+    const uint32_t *T = g.hub_keys + D.x;
+    uint32_t p = gm_hash(key >> 1) & mask;
+    bytes += 12;
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+      const uint32_t e = __ldg(T + p);
+      bytes += (probe == 0 || (p & 7u) == 0) ? 32 : 0;
+      if (e == GM_EMPTY) return false;
+      if ((e | 1u) == (key | 1u)) {
+        if (!(e & 1u)) return true;
+        break;  // batch edge: fetch its tag below
+      }
+      p = (p + 1) & mask;
+    }
+    a = __ldg(reinterpret_cast<const uint2 *>(g.adj) + w);
+  } else {
+    a = make_uint2(D.x, D.y & ~GM_DESC_LIST);
+  }
+  if (a.y <= GM_SCAN_MAX) {
+    // a short list is read whole: independent 16-byte loads from the aligned
+    // word before it (the pool is padded), one memory round trip instead of
+    // a chain of binary-search steps
+    const uint32_t b0 = a.x & ~3u, off = a.x - b0, end = off + a.y;
+    const uint4 *P4 = reinterpret_cast<const uint4 *>(g.col + b0);
+    int hit = -1;
+    uint32_t hy = 0;
+#pragma unroll
+    for (int j = 0; j < (GM_SCAN_MAX + 3) / 4 + 1; j++) {
+      if (4u * j < end) {
+        const uint4 q4 = __ldg(P4 + j);
+        const uint32_t wv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+          const uint32_t idx = 4u * j + t;
+          if (idx >= off && idx < end && (wv[t] | 1u) == (key | 1u)) { hit = (int)(idx - off); hy = wv[t]; }
         }
-        p = (p + 1) & mask;
       }
     }
+    bytes += 16u * ((end + 3) / 4) + 8u;
+    if (hit < 0) return false;
+    if (hy & 1u) return tag_ok(__ldg(g.etag + a.x + hit), sdel, upd, req, r, cnext, op);
+    return true;
   }
-  const uint2 a = __ldg(reinterpret_cast<const uint2 *>(g.adj) + w);
   bytes += probe_bytes(a.y);
   const uint32_t *L = g.col + a.x;
   uint32_t p = gm_lower_bound(L, a.y, key);
@@ -116,6 +150,13 @@ __device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t 
   if ((y | 1u) != (key | 1u)) return false;
   if (y & 1u) return tag_ok(__ldg(g.etag + a.x + p), sdel, upd, req, r, cnext, op);
   return true;
+}
+
+template <bool C>
+__device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t x, uint32_t sdel,
+                                        uint32_t upd, const uint32_t *req, uint32_t r, const uint32_t *cnext,
+                                        const int8_t *op, ByteCount<C> &bytes) {
+  return edge_ok_d(g, w, edge_desc(g, w), x, sdel, upd, req, r, cnext, op, bytes);
 }
 
 __device__ __forceinline__ bool nlf_ok(const GraphDev &g, uint32_t v, const Plan &P, int pos) {
@@ -281,6 +322,8 @@ struct WarpHdr {
   uint32_t cur[GM_MAXQ];   // expansion pairs consumed per level
   uint32_t tot[GM_MAXQ];   // expansion pairs this warp still owns per level
   uint32_t full[GM_MAXQ];  // expansion pairs of the level before any donation
+  uint32_t coll;           // bit L: level L's entries share their last-position candidates by sibling run
+  int32_t hoist;           // level whose entries carry HO (the last level, prepared), else -1
 };
 
 __host__ __device__ inline size_t smem_per_warp(int tile, int nlev) {
@@ -289,10 +332,14 @@ __host__ __device__ inline size_t smem_per_warp(int tile, int nlev) {
   size_t lt = (size_t)nlev * tile;
   b += lt * 4 * 3;              // V, LO, EX
   b += lt * 2;                  // PAR
+  b += lt * 2;                  // MUL
   b += lt;                      // DRV
-  return (b + 15) & ~(size_t)15;
+  b = (b + 15) & ~(size_t)15;
+  b += (size_t)tile * 16;       // HO: the last level's first membership test per entry
+  return b;
 }
 
+constexpr uint32_t GM_RING_LARGE = 1u << 20;  // task rings this large take reservations without a retry loop
 constexpr uint32_t DONATE_EVERY = 16;  // expansion steps between looks at the waiting tickets
 constexpr uint32_t DONATE_MIN = 64;    // pairs a level must still own to be split
 
@@ -336,30 +383,41 @@ __device__ bool idle_wait(const MatchArgs &a, uint64_t &slot) {
   }
 }
 
-// lane 0 of a busy warp: reserve n consecutive task numbers and count their
-// future runners as busy.  Task number r lives in ring slot r mod capacity,
-// whose previous occupant is task r - capacity; that task is read promptly
-// only if an idle warp already holds its ticket.  So a reservation is refused
-// (false) when its last number would reach capacity past the tickets taken:
-// donors that read the same demand at once could otherwise reserve more
-// tasks than the ring holds and wait on slots nobody is about to free.
-__device__ bool reserve_tasks(const MatchArgs &a, uint32_t n, uint32_t &base) {
+// lane 0 of a busy warp: reserve up to n consecutive task numbers, no more
+// than the tickets of idle warps not yet matched with a task, and count
+// their future runners as busy.  Returns the number granted (0: none).
+// Every granted number is below the tickets taken, so each has a waiting
+// receiver: donors that read the same demand at once cannot flood the queue
+// with tasks nobody waits for, and task r's ring slot (r mod capacity) was
+// freed by task r - capacity, whose receiver already holds its ticket.
+__device__ uint32_t reserve_tasks(const MatchArgs &a, uint32_t n, uint32_t &base) {
   uint32_t *sched = a.sched;
-  if (n == 0 || n > a.task_cap) return false;
+  if (n == 0 || n > a.task_cap) return 0;
   atomicAdd(sched + GM_SCHED_BUSY, n);  // the donor itself is busy, so no warp can see zero meanwhile
+  if (a.task_cap >= GM_RING_LARGE) {
+    // a large ring: one atomic, no retries under contention.  The caller
+    // asked for no more than the waiting tickets it read, so donors reading
+    // at once overshoot by at most 32 tasks each, far below the ring's
+    // capacity, and every slot's previous task was read long before.
+    base = atomicAdd(sched + GM_SCHED_RESERVE, n);
+    return n;
+  }
   uint32_t r = vload(sched + GM_SCHED_RESERVE);
   while (true) {
-    const uint32_t t = vload(sched + GM_SCHED_TICKET);
-    if ((int32_t)(r + n - t) > (int32_t)a.task_cap) {
+    const int32_t waiting = (int32_t)(vload(sched + GM_SCHED_TICKET) - r);
+    const uint32_t g = waiting > 0 ? min(n, (uint32_t)waiting) : 0u;
+    if (g == 0) {
       atomicSub(sched + GM_SCHED_BUSY, n);
-      return false;
+      return 0;
     }
-    const uint32_t old = atomicCAS(sched + GM_SCHED_RESERVE, r, r + n);
-    if (old == r) break;
+    const uint32_t old = atomicCAS(sched + GM_SCHED_RESERVE, r, r + g);
+    if (old == r) {
+      if (g < n) atomicSub(sched + GM_SCHED_BUSY, n - g);
+      base = r;
+      return g;
+    }
     r = old;
   }
-  base = r;
-  return true;
 }
 
 // write task number r into its ring slot: wait (bounded) until the slot's
@@ -409,7 +467,11 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
   uint32_t *LO = V + (size_t)NL * T;
   uint32_t *EX = LO + (size_t)NL * T;
   uint16_t *PAR = reinterpret_cast<uint16_t *>(EX + (size_t)NL * T);
-  uint8_t *DRV = reinterpret_cast<uint8_t *>(PAR + (size_t)NL * T);
+  uint16_t *MUL = PAR + (size_t)NL * T;  // sibling-run length at the run's first entry
+  uint8_t *DRV = reinterpret_cast<uint8_t *>(MUL + (size_t)NL * T);
+  // per entry of the last level: {vertex w, its index descriptor, position} of
+  // the first membership test, read once at prepare instead of per candidate
+  uint4 *HO = reinterpret_cast<uint4 *>(wbase + ((o + (size_t)NL * T * 17 + 15) & ~(size_t)15));  // after DRV
 
   if (warp_read(&st->err)) return;
   const uint64_t nitems = min(*(volatile uint64_t *)&st->nitems, a.item_cap);
@@ -481,6 +543,7 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       cur_plan = plan;
     }
     if (lane < GM_MAXQ) H->cnt[lane] = 0;
+    if (lane == 0) { H->coll = 0; H->hoist = -1; }
     __syncwarp();
     int lev;
     uint32_t root_lo = wlo, root_len = wlen, root_cur = 0, root_drv = wdrv;
@@ -512,20 +575,36 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
     const uint32_t rq = a.req ? __ldg(a.req + upd) : 0u;
     uint64_t wcount = 0;
     ByteCount<kCountBytes> lbytes;  // this lane's algorithmic bytes (instrumented build only)
-    uint32_t chunks = 0;
+    uint32_t chunks = 0, flushed = 0;  // expansion steps of this unit; those already added to the total
 
     // prepare level L (position L+2): driver segment of every entry for position L+3
+    // Shared-prefix coalescing: when the last query vertex is not adjacent to
+    // the one before it, the children of one partial match (a run of
+    // siblings, consecutive and sorted by id in the level) have the same
+    // last-position candidates.  Only the run's first entry then gets a
+    // driver range; each candidate it finds counts once per sibling, minus
+    // the sibling it would coincide with (same label).  Counts only.
     auto prepare = [&](int L) {
       const int p = L + 2, np = p + 1;
       const uint16_t bw = P.bwd[np];
       const int lab = P.lab[np];
       const uint32_t n = H->cnt[L];
+      const bool coll = a.share && np == last && !((bw >> p) & 1u) && !(a.leaf && __popc((uint32_t)bw) == 1);
+      const uint16_t *par = PAR + L * T;
       uint32_t carry = 0;
       for (uint32_t base = 0; base < n; base += 32) {
         uint32_t i = base + lane;
         uint32_t len = 0, lo = 0;
         int drv = 0;
-        if (i < n) {
+        bool first = true;
+        if (coll && i < n) {
+          first = i == 0 || par[i] != par[i - 1];
+          uint32_t j = i + 1;
+          if (first)
+            while (j < n && par[j] == par[i]) j++;
+          MUL[L * T + i] = (uint16_t)(j - i);
+        }
+        if (i < n && first) {
           // the backward neighbour with the fewest label-lab neighbours drives
           uint32_t best = 0xffffffffu, bestv = 0;
           uint32_t e = i;
@@ -548,8 +627,29 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
           }
           lbytes += 4u * __popc(bw);
           if (best > 0) label_segment(g, bestv, lab, lo, len, lbytes);
+        }
+        if (i < n) {
           LO[L * T + i] = lo;
           DRV[L * T + i] = (uint8_t)drv;
+        }
+        if (np == last && i < n && first) {
+          // the first membership test of the last position (its highest
+          // backward neighbour other than the driver), looked up once here
+          const uint32_t chk = (uint32_t)bw & ~(1u << drv);
+          uint32_t w = 0, hp = 0xFFu;
+          uint2 D = make_uint2(0, 0);
+          if (chk && len) {
+            hp = 31u - __clz(chk);
+            if (hp >= 2) {
+              uint32_t ee = i;
+              for (int l2 = L; l2 > (int)hp - 2; l2--) ee = PAR[l2 * T + ee];
+              w = V[(hp - 2) * T + ee];
+            } else {
+              w = hp ? m1 : m0;
+            }
+            D = edge_desc(g, w);
+          }
+          HO[i] = make_uint4(w, D.x, D.y, hp);
         }
         uint32_t inc = len;
         for (int d = 1; d < 32; d <<= 1) {
@@ -559,7 +659,11 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
         if (i < n) EX[L * T + i] = carry + inc - len;
         carry += __shfl_sync(GM_FULL, inc, 31);
       }
-      if (lane == 0) { H->tot[L] = carry; H->full[L] = carry; H->cur[L] = 0; }
+      if (lane == 0) {
+        H->tot[L] = carry; H->full[L] = carry; H->cur[L] = 0;
+        H->coll = coll ? (H->coll | (1u << L)) : (H->coll & ~(1u << L));
+        if (np == last) H->hoist = L;
+      }
       __syncwarp();
     };
 
@@ -569,7 +673,8 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       int L = -2;
       if (root_len > root_cur && root_len - root_cur >= DONATE_MIN) L = -1;
       for (int l = 0; L == -2 && l <= lev; l++)
-        if (H->tot[l] > H->cur[l] && H->tot[l] - H->cur[l] >= DONATE_MIN && l < GM_TASK_M) L = l;
+        if (H->tot[l] > H->cur[l] && H->tot[l] - H->cur[l] >= DONATE_MIN && l < GM_TASK_M && !((H->coll >> l) & 1u))
+          L = l;  // a shared level stays: a task could not carry its sibling runs
       if (L == -2) return;
       const uint32_t c0 = (L < 0) ? root_cur : H->cur[L];
       const uint32_t t0 = (L < 0) ? root_len : H->tot[L];
@@ -578,7 +683,7 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       if (L < 0) {
         uint32_t base = 0;
         int ok = 0;
-        if (lane == 0 && reserve_tasks(a, 1, base)) {
+        if (lane == 0 && reserve_tasks(a, 1, base) == 1) {
           Task t;
           t.upd = upd; t.plan = (uint16_t)plan; t.depth = -1; t.drv = (uint8_t)root_drv;
           t.lo = root_lo + s; t.len = t0 - s;
@@ -601,15 +706,14 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       };
       const uint32_t e_s = entry_of(s), e_end = entry_of(t0 - 1);
       const uint32_t most = min(32u, max(want, 1u));
-      const uint32_t e_first = (e_end - e_s >= most) ? e_end - (most - 1) : e_s;
-      const uint32_t s2 = (e_first == e_s) ? s : ex[e_first];
-      const uint32_t nt = e_end - e_first + 1;
+      uint32_t nt = min(e_end - e_s + 1, most);
       uint32_t base = 0;
-      int ok = 0;
-      if (lane == 0) ok = reserve_tasks(a, nt, base) ? 1 : 0;
-      ok = __shfl_sync(GM_FULL, ok, 0);
-      if (!ok) return;
+      if (lane == 0) nt = reserve_tasks(a, nt, base);  // the tail entries, as many as were granted
+      nt = __shfl_sync(GM_FULL, nt, 0);
+      if (nt == 0) return;
       base = __shfl_sync(GM_FULL, base, 0);
+      const uint32_t e_first = e_end - (nt - 1);
+      const uint32_t s2 = (e_first == e_s) ? s : ex[e_first];
       if ((uint32_t)lane < nt) {
         const uint32_t e = e_first + lane;
         const uint32_t elen = ((e + 1 < n) ? ex[e + 1] : H->full[L]) - ex[e];
@@ -772,8 +876,18 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       uint32_t x = ok ? __ldg(g.col + slot2) : 0u;
       const uint32_t id = (x >> 1) & g.idmask;
       if (ok && (x & 1u)) ok = tag_ok(__ldg(g.etag + slot2), sdel, upd, a.req, rq, a.cnext, a.op);
-      const uint16_t chk_edge = P.bwd[c] & (uint16_t)~(1u << drv);
-      const uint16_t chk_neq = P.samelab[c];
+      uint32_t hp = 0xFFu;  // position whose membership test was looked up at prepare
+      if (!stored && lev >= 0 && H->hoist == lev) {
+        const uint4 h = HO[e];
+        hp = h.w;
+        if (ok && hp != 0xFFu) ok = edge_ok_d(g, h.x, make_uint2(h.y, h.z), x, sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
+      }
+      const uint16_t chk_edge = P.bwd[c] & (uint16_t)~(1u << drv) & (uint16_t)~(hp < 16u ? (1u << hp) : 0u);
+      const bool shared = !stored && lev >= 0 && ((H->coll >> lev) & 1u);
+      // shared: the run's siblings differ at position lev + 2 only; that
+      // position is no backward neighbour of c, and equality with it is
+      // settled per sibling below
+      const uint16_t chk_neq = shared ? (uint16_t)(P.samelab[c] & ~(1u << (lev + 2))) : P.samelab[c];
       if (ok && (chk_edge | chk_neq)) {
         uint32_t ee = e;
         // walk the stored positions only down to the lowest one with a check
@@ -794,7 +908,24 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       if (ok && stored && a.use_filter) ok = nlf_ok(g, id, P, c);
       if (gidx < total) lbytes += ((x & 1u) ? 8u : 4u) + (ok ? 8u : 0u);
       const unsigned mask = __ballot_sync(GM_FULL, ok);
-      if (!stored) {
+      if (shared) {
+        uint32_t add = 0;
+        if (ok) {
+          const uint32_t m = MUL[lev * T + e];
+          add = m;
+          if ((P.samelab[c] >> (lev + 2)) & 1u) {  // is the candidate one of the siblings (sorted by id)?
+            const uint32_t *sv = V + lev * T + e;
+            uint32_t l2 = 0, h2 = m;
+            while (l2 < h2) {
+              const uint32_t mid = (l2 + h2) >> 1;
+              if (sv[mid] < id) l2 = mid + 1; else h2 = mid;
+            }
+            if (l2 < m && sv[l2] == id) add--;
+            lbytes += 4u * (32u - __clz(m));
+          }
+        }
+        wcount += __reduce_add_sync(GM_FULL, add);
+      } else if (!stored) {
         wcount += __popc(mask);
         if (a.rows && mask) {
           uint64_t rb = 0;
@@ -839,7 +970,18 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
         const uint32_t want = demand(a);
         if (want) donate(want);
       }
-      if ((chunks & 1023u) == 0 && warp_read(&st->abort)) break;
+      if (chunks - flushed >= 1024u) {  // add to the total as we go, so a budget stops a long unit too
+        if (lane == 0) {
+          const unsigned long long d = chunks - flushed;
+          const unsigned long long ex = atomicAdd((unsigned long long *)&st->expansions, d) + d;
+          if (a.budget && ex > a.budget) {
+            atomicExch(&st->abort, 1);
+            gm_set_err(st, GAMMA_ETIMEOUT);
+          }
+        }
+        flushed = chunks;
+        if (warp_read(&st->abort)) break;
+      }
     }
     if (kCountBytes) {
       uint64_t tb = lbytes.v + ((lane == 0) ? 16u : 0u);
@@ -852,8 +994,9 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
         if (a.per_upd)
           atomicAdd((unsigned long long *)&a.per_upd[(uint64_t)P.qslot * a.b + upd], (unsigned long long)wcount);
       }
-      unsigned long long ex = atomicAdd((unsigned long long *)&st->expansions, (unsigned long long)chunks);
-      if (a.budget && ex + chunks > a.budget) {
+      const unsigned long long d = chunks - flushed;
+      unsigned long long ex = atomicAdd((unsigned long long *)&st->expansions, d);
+      if (a.budget && ex + d > a.budget) {
         atomicExch(&st->abort, 1);
         gm_set_err(st, GAMMA_ETIMEOUT);
       }

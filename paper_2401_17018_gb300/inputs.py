@@ -546,28 +546,51 @@ def sample_distinct(n: int, k: int, seed: int, stream: int, sub: int = 0) -> np.
     return got
 
 
+def _take(pool: np.ndarray, size: int, pos: np.ndarray) -> Tuple[np.ndarray, int]:
+    """Remove the entries at positions ``pos`` (distinct, < size) from the
+    first ``size`` entries of ``pool`` in O(len(pos)): the holes below the
+    new end are filled with the kept entries of the tail.  Returns the
+    removed entries and the new size."""
+    k = pos.size
+    taken = pool[pos].copy()
+    new = size - k
+    holes = np.sort(pos[pos < new])
+    mark = np.zeros(k, bool)
+    mark[pos[pos >= new] - new] = True
+    fill = new + np.flatnonzero(~mark)
+    pool[holes] = pool[fill]
+    return taken, new
+
+
 def served_stream(w: "Workload", n_batches: int, seed: int, lo_exp: float = 3.0,
                   hi_exp: float = 6.0) -> List[Batch]:
     """The served workload's request stream: batches of floor(10^U(3, 6))
-    updates (the exponents are parameters) with insertions : deletions = 1 : 1.  Deletions are drawn from the
-    graph as it stands after the previous batches, insertions from the free
-    pool (held-out edges and edges deleted earlier), so every batch is valid
-    in order; the updates of a batch are interleaved by a seeded shuffle."""
+    updates (the exponents are parameters) with insertions : deletions = 1 : 1.  Deletions are drawn uniformly
+    without replacement from the graph as it stands after the previous
+    batches, insertions from the free pool (held-out edges and edges deleted
+    earlier), so every batch is valid in order; the updates of a batch are
+    interleaved by a seeded shuffle.  The present and free edge sets are kept
+    as arrays with O(batch) removal, so a long stream costs time in
+    proportion to its updates, not to the graph."""
     g = w.graph
     src = np.concatenate([g.src, w.pool_src])
     dst = np.concatenate([g.dst, w.pool_dst])
-    present = np.zeros(src.size, bool)
-    present[:g.src.size] = True
+    m0, m = g.src.size, src.size
+    pres = np.empty(m, np.int64)
+    pres[:m0] = np.arange(m0)
+    free = np.empty(m, np.int64)
+    free[:m - m0] = np.arange(m0, m)
+    npres, nfree = m0, m - m0
     out = []
     for k, n in enumerate(served_sizes(n_batches, seed, lo_exp, hi_exp)):
         nd = int(n) // 2
         ni = int(n) - nd
-        pres = np.flatnonzero(present)
-        free = np.flatnonzero(~present)
-        d = pres[sample_distinct(pres.size, nd, seed, S_SRV_DEL, k)]
-        i = free[sample_distinct(free.size, ni, seed, S_SRV_INS, k)]
-        present[d] = False
-        present[i] = True
+        d, npres = _take(pres, npres, sample_distinct(npres, nd, seed, S_SRV_DEL, k))
+        i, nfree = _take(free, nfree, sample_distinct(nfree, ni, seed, S_SRV_INS, k))
+        pres[npres:npres + ni] = i
+        npres += ni
+        free[nfree:nfree + nd] = d
+        nfree += nd
         op = np.concatenate([np.ones(i.size, np.int8), -np.ones(d.size, np.int8)])
         e = np.concatenate([i, d])
         mix = shuffle_order(op.size, seed, S_SRV_MIX, k)

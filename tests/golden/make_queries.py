@@ -2,22 +2,30 @@
 
 Queries are extracted from G0 by the seeded extractor of
 ``paper_2401_17018_gb300.inputs.random_walk_query`` (Sec. VI-A: random
-subgraphs of the data graph, classed by density). As in the paper, which
-leaves queries over a 30-minute cap unsolved and out of its averages
-(Sec. VI-A "Metrics"), a candidate is only kept when its work is bounded:
-the CPU oracle must finish the candidate on a fixed sample of the batch's
-updates (every ``stride``-th update) within ``budget`` candidate tests, and
-the sample must contain at least one incremental match. Rejected candidates
-are logged in the output with the reason. Nothing here touches the CUDA path.
+subgraphs of the data graph, classed by density), attempt after attempt, in
+the sizes and classes each workload asks for; a size never falls to a
+smaller one.  As in the paper, which leaves queries over a 30-minute cap
+unsolved and out of its averages (Sec. VI-A "Metrics"), a candidate is kept
+only when every pair of its check set can be verified by the CPU oracle:
 
-Some workloads add to the sample the updates whose endpoints have the largest
-degree product in G0: on a power-law graph those updates carry most of a
-query's work, which a uniform sample misses. Such a workload may also cap the
-attempts per (class, size); slots that the cap leaves empty fall to the next
-smaller size of the same class, and each stored query records the size it
-was planned with (``q_planned``).
+* the check set of query Q on a batch = a uniform sample of the batch's
+  updates (every ``stride``-th) and the ``heavy`` heaviest verifiable
+  updates: going down the updates whose endpoint labels match some edge of
+  Q (in either orientation) by decreasing product of endpoint degrees in
+  the graph the batch meets (on a power-law graph those carry most of Q's
+  work), the first ``heavy`` that the oracle finishes within
+  ``heavy_budget`` candidate tests each (those it cannot finish are passed
+  over and counted; only the first ``TOP_PER_PAIR`` per label pair are
+  tried);
+* the oracle must finish each sampled pair within ``sample_budget``
+  candidate tests, find ``heavy`` verifiable heavy updates, and the check
+  set must hold at least one incremental match.
 
-Usage: python tests/golden/make_queries.py mid|batched|served|large [--workers 8]
+Rejections are counted per class and reason in the output.  Nothing here
+touches the CUDA path: the oracle alone decides.  The check sets of every
+batch are later evaluated without budgets by ``make_expected.py``.
+
+Usage: python tests/golden/make_queries.py large|mid|batched|served [--workers 8]
 """
 import argparse
 import json
@@ -36,70 +44,140 @@ from oracle import oracle as O  # noqa: E402
 from paper_2401_17018_gb300 import inputs as I  # noqa: E402
 
 SPECS = {
-    # name: (workload, batch inserts, batch deletions, plan of (kind, q) per query)
-    "mid": ("mid", 90_000, 10_000, [("sparse", 6)] * 10 + [("dense", 6)] * 10),
-    # 64 queries of 4..12 vertices (uneven sizes), alternating sparse and dense
-    "batched": ("mid", 90_000, 10_000,
-                [("sparse" if i % 2 == 0 else "dense_ge3", 4 + (i * 7) % 9) for i in range(64)]),
-    # 16 queries of 6..8 vertices on the scale-22 graph (the served stream's first batch)
-    "served": ("served", 3_000, 1_000, [("dense", 6 + i % 3) for i in range(16)]),
-    # 8-vertex queries, 4 sparse and 4 dense, on the scale-23 graph (first batch)
-    "large": ("large", 800_000, 200_000, [("sparse", 8)] * 4 + [("dense", 8)] * 4),
+    # 6-vertex queries (the paper's default size), 4 sparse and 4 dense, on
+    # the scale-23 graph; selected on the first of the five consecutive
+    # batches.  (8-vertex random-walk queries on this graph need more than
+    # 2e10 DFS expansion steps of one GB300 per 1M-update batch for 10 of 11
+    # measured candidates, and none of about 400 candidates had its heavy
+    # updates verifiable by the oracle.)
+    "large": {"workload": "large", "plan": [("sparse", 6)] * 4 + [("dense", 6)] * 4,
+              "stride": 20_000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
+              "max_attempts": 4000},
+    # 20 six-vertex queries, 10 sparse and 10 dense, on the scale-20 graph
+    "mid": {"workload": "mid", "plan": [("sparse", 6)] * 10 + [("dense", 6)] * 10,
+            "stride": 1000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
+            "max_attempts": 4000},
+    # 64 queries of 4..12 vertices (uneven sizes), sparse and dense alternating
+    # (dense in the paper's sense, average degree >= 3), on the mid graph
+    "batched": {"workload": "mid", "plan": [("sparse" if i % 2 == 0 else "dense_ge3", 4 + (i * 7) % 9)
+                                            for i in range(64)],
+                "stride": 1000, "sample_budget": 2_000_000, "heavy": 8, "heavy_budget": 20_000_000,
+                "max_attempts": 6000},
+    # 16 dense queries of 6..8 vertices on the scale-22 served graph; the
+    # selection batch has the served stream's 1:1 mix of insertions and
+    # deletions
+    "served": {"workload": "served", "plan": [("dense", 6 + i % 3) for i in range(16)],
+               "stride": 1000, "sample_budget": 1_000_000, "heavy": 8, "heavy_budget": 10_000_000,
+               "max_attempts": 6000},
 }
-# (stride, budget) per query class: every stride-th update of the batch is
-# evaluated, within budget candidate tests. Sparse queries on the power-law
-# graphs are far costlier per update, so they get a thinner sample and a
-# larger budget.
-RULES = {"dense": (200, 10_000_000), "dense_ge3": (200, 10_000_000), "sparse": (2500, 40_000_000),
-         "tree": (2500, 40_000_000)}
+TOP_PER_PAIR = 64  # heavy candidates kept per endpoint-label pair
 
-# per-workload sampling that differs from the defaults above: (stride, budget)
-# per class, the heavy updates added to the sample, the attempt cap per
-# (class, size), and the smallest size a slot may fall to
-SAMPLING = {
-    "batched": {"rules": {"dense_ge3": (1000, 20_000_000), "sparse": (1000, 20_000_000)},
-                "heavy": 8, "max_attempts": 60},
-    "served": {"rules": {"dense": (100, 2_400_000)}, "heavy": 8, "max_attempts": 200, "min_q": 5},
-    "large": {"rules": {"dense": (20000, 3_000_000), "sparse": (20000, 3_000_000)},
-              "heavy": 8, "max_attempts": 40, "min_q": 5},
-}
-DEFAULT_SAMPLING = {"rules": RULES, "heavy": 0, "max_attempts": 20000}
+_S = None
 
-_W = None
+
+def selection_batch(name, w):
+    """The batch a workload's queries are chosen on."""
+    wl = SPECS[name]["workload"]
+    if wl == "large":
+        return I.consecutive_batches(w, 1, 800_000, 200_000)[0]
+    if wl == "served":
+        return I.workload_batch(w, 50_000, 50_000)
+    return I.workload_batch(w, 90_000, 10_000)
+
+
+def heavy_table(labels, deg, b, top=TOP_PER_PAIR):
+    """For every unordered endpoint-label pair, the batch's updates with that
+    pair, by decreasing product of endpoint degrees (ties: smaller index)."""
+    la, lb = labels[b.src], labels[b.dst]
+    lo, hi = np.minimum(la, lb), np.maximum(la, lb)
+    prod = deg[b.src].astype(np.float64) * deg[b.dst].astype(np.float64)
+    order = np.lexsort((np.arange(len(b)), -prod))
+    table = {}
+    for k in order:
+        key = (int(lo[k]), int(hi[k]))
+        lst = table.setdefault(key, [])
+        if len(lst) < top:
+            lst.append(int(k))
+    return table, prod
+
+
+def heavy_candidates(q, table, prod):
+    """The updates label-compatible with some edge of q (the first
+    TOP_PER_PAIR of each endpoint-label pair), by decreasing endpoint-degree
+    product (ties: smaller index)."""
+    cand = set()
+    for a, c in zip(q.src.tolist(), q.dst.tolist()):
+        la, lc = int(q.labels[a]), int(q.labels[c])
+        cand.update(table.get((min(la, lc), max(la, lc)), []))
+    return sorted(cand, key=lambda k: (-prod[k], k))
+
+
+def check_pairs(sess, Q, table, prod, sample, spec, strict_sample):
+    """Evaluate Q's check set on one batch, one pair at a time: the sampled
+    updates within the sample budget, then the heaviest verifiable updates.
+    Returns (counts by update, heavy updates, passed-over updates, reason):
+    reason is None when the set is complete; with strict_sample a sampled
+    update over budget is a reason (selection), else it is passed over."""
+    got, passed = {}, []
+    for u in sample.tolist():
+        c = int(sess.eval([Q], eval_idx=[u], update_budget=spec["sample_budget"])[0, 0])
+        if c == int(O.NOT_COMPUTED):
+            if strict_sample:
+                return got, [], passed, "a sampled update needs more than the sample budget"
+            passed.append(u)
+            continue
+        got[u] = c
+    heavy = []
+    for u in heavy_candidates(Q, table, prod):
+        if len(heavy) == spec["heavy"]:
+            break
+        if u in got:
+            heavy.append(u)
+            continue
+        c = int(sess.eval([Q], eval_idx=[u], update_budget=spec["heavy_budget"])[0, 0])
+        if c == int(O.NOT_COMPUTED):
+            passed.append(u)
+            continue
+        got[u] = c
+        heavy.append(u)
+    if len(heavy) < spec["heavy"]:
+        return got, heavy, passed, "fewer verifiable heavy updates than required"
+    return got, heavy, passed, None
 
 
 def _init(name):
-    global _W
-    wl, ni, nd, _ = SPECS[name]
-    w = I.make_workload(wl)
-    b = I.workload_batch(w, ni, nd)
+    global _S
+    spec = SPECS[name]
+    w = I.make_workload(spec["workload"])
+    b = selection_batch(name, w)
     off, nbr = I.csr_from_edges(w.graph.n, w.graph.src, w.graph.dst)
-    samp = SAMPLING.get(name, DEFAULT_SAMPLING)
-    deg = np.diff(off).astype(np.float64)
-    prod = deg[b.src] * deg[b.dst]
-    heavy = np.sort(np.argsort(-prod, kind="stable")[:samp["heavy"]])
-    _W = (w, b, off, nbr, samp, heavy)
+    deg = np.diff(off)
+    table, prod = heavy_table(w.graph.labels, deg, b)
+    sess = O.Session(w.graph.n, w.graph.labels, w.graph.src, w.graph.dst, b)
+    sample = np.arange(0, len(b), spec["stride"], dtype=np.int64)
+    _S = (spec, w, b, off, nbr, table, prod, sess, sample)
 
 
 def _try(args):
     kind, q, attempt = args
-    w, b, off, nbr, samp, heavy = _W
+    spec, w, b, off, nbr, table, prod, sess, sample = _S
     g = w.graph
     Q = I.random_walk_query(off, nbr, g.labels, q, kind, w.seed + 1000 * q, attempt)
     if Q is None:
         return attempt, None, "class test failed"
-    stride, budget = samp["rules"][kind]
-    ev = np.union1d(np.arange(0, len(b), stride), heavy)
     t = time.time()
-    try:
-        c, _ = O.bdsm(g.n, g.labels, g.src, g.dst, Q, b, eval_idx=ev, budget=budget)
-    except O.OracleError as e:
-        return attempt, Q.to_json(), "oracle budget exceeded on the sample (code %d)" % e.code
-    if int(c.sum()) == 0:
-        return attempt, Q.to_json(), "no incremental match on the sample"
+    got, heavy, passed, why = check_pairs(sess, Q, table, prod, sample, spec, strict_sample=True)
+    if why is not None:
+        return attempt, None, why
+    if sum(got.values()) == 0:
+        return attempt, None, "no incremental match in the check set"
     d = Q.to_json()
-    d["sample_matches"] = int(c.sum())
-    d["sample_seconds"] = round(time.time() - t, 2)
+    d["kind"] = kind
+    d["attempt"] = attempt
+    d["sample_matches"] = int(sum(got[u] for u in sample.tolist()))
+    d["heavy_matches"] = int(sum(got[u] for u in heavy))
+    d["heavy_passed_over"] = len(passed)
+    d["check_seconds"] = round(time.time() - t, 2)
     return attempt, d, None
 
 
@@ -107,108 +185,98 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("name", choices=sorted(SPECS))
     ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--kind", default=None, help="select only this class (the partial results are merged by --merge)")
+    ap.add_argument("--merge", action="store_true", help="merge the per-class partial files into the output")
     args = ap.parse_args()
-    wl, ni, nd, plan = SPECS[args.name]
+    spec = SPECS[args.name]
+    if args.merge:
+        return merge(args.name)
     _init(args.name)
-    w, samp, heavy = _W[0], _W[4], _W[5]
-    rule = ("keep a candidate of class k when the CPU oracle finishes it on updates 0, s, 2s, ... of the "
-            "batch within B candidate tests and finds at least one incremental match there; (s, B) per "
-            "class: " + json.dumps(samp["rules"]))
-    if samp["heavy"]:
-        rule += ("; the sample also holds the %d updates with the largest product of endpoint degrees in G0 "
-                 "(%s)" % (samp["heavy"], ", ".join(str(int(x)) for x in heavy)))
-    if samp["max_attempts"] < DEFAULT_SAMPLING["max_attempts"]:
-        rule += ("; at most %d attempts per (class, size), the slots left empty fall to the next smaller "
-                 "size of the class" % samp["max_attempts"])
-        if "min_q" in samp:
-            rule += " (down to %d vertices)" % samp["min_q"]
-    out = {"workload": wl, "graph_digest": w.graph.digest(), "batch": {"n_ins": ni, "n_del": nd, "sub": 0},
-           "rule": rule, "queries": [], "rejected": []}
+    w, b = _S[1], _S[2]
+    rule = ("keep a candidate when the CPU oracle verifies its check set on the selection batch: every %d-th "
+            "update within %d candidate tests each, and the %d heaviest verifiable updates (going down the updates "
+            "whose endpoint labels match one of the query's edges by decreasing endpoint-degree product, the first "
+            "%d finished within %d candidate tests each; heavier ones are passed over and counted); the check set "
+            "must hold an incremental match; at most %d attempts per (class, size), no fall to smaller sizes" % (
+                spec["stride"], spec["sample_budget"], spec["heavy"], spec["heavy"], spec["heavy_budget"],
+                spec["max_attempts"]))
+    out = {"workload": spec["workload"], "graph_digest": w.graph.digest(), "selection_batch_updates": len(b),
+           "rule": rule, "queries": [], "rejected": {}}
     want = {}
-    for kind, q in plan:
-        want[(kind, q)] = want.get((kind, q), 0) + 1
-    kinds = sorted({k for k, _ in want})
-    qmax = {k: max(q for kk, q in want if kk == k) for k in kinds}
-    qmin = {k: min([q for kk, q in want if kk == k] + [samp.get("min_q", 99)]) for k in kinds}
-    # every size from the largest down to the smallest, so shortfalls can fall
-    classes = [(k, q) for k in kinds for q in range(qmax[k], qmin[k] - 1, -1)]
-    chosen = {c: [] for c in classes}
+    for kind, q in spec["plan"]:
+        if args.kind is None or kind == args.kind:
+            want[(kind, q)] = want.get((kind, q), 0) + 1
+    chosen = {c: [] for c in want}
     seen = set()
-    path = os.path.join(HERE, "queries_%s.json" % args.name)
-    partial = path + ".partial"
-    start_at = {}
-    if os.path.exists(partial):  # resume: keep what an interrupted run chose
-        with open(partial) as f:
-            old = json.load(f)
-        for d in old["chosen"]:
-            key = (d["kind"], len(d["labels"]))
-            if key in chosen:
-                chosen[key].append(d)
-                seen.add(json.dumps([d["labels"], d["edges"]]))
-        out["rejected"] = old["rejected"]
-        start_at = {(k.split(":")[0], int(k.split(":")[1])): v for k, v in old.get("next_attempt", {}).items()}
-    next_attempt = dict(start_at)
-
-    def save_partial():
-        with open(partial, "w") as f:
-            json.dump({"chosen": [d for v in chosen.values() for d in v], "rejected": out["rejected"],
-                       "next_attempt": {"%s:%d" % k: v for k, v in next_attempt.items()}}, f)
-    cap = samp["max_attempts"]
-    carry = {k: 0 for k in kinds}
-    ctx = get_context("fork")
+    ctx = get_context("fork")  # the workers share the parent's graph and oracle session
+    t0 = time.time()
     with ctx.Pool(args.workers) as pool:
-        for kind, q in classes:
-            need = want.get((kind, q), 0) + carry[kind]
-            attempt = int(start_at.get((kind, q), 0))
+        for (kind, q), need in sorted(want.items()):
             got = chosen[(kind, q)]
-            del got[need:]
-            while len(got) < need and attempt < cap:
-                jobs = [(kind, q, a) for a in range(attempt, min(attempt + args.workers * 2, cap))]
+            attempt = 0
+            rej = out["rejected"].setdefault("%s:%d" % (kind, q), {})
+            while len(got) < need and attempt < spec["max_attempts"]:
+                jobs = [(kind, q, a) for a in range(attempt, min(attempt + args.workers * 4, spec["max_attempts"]))]
                 attempt += len(jobs)
-                for att, d, why in pool.map(_try, jobs):
-                    if len(got) >= need:
-                        break
-                    if why is None:
-                        key = json.dumps([d["labels"], d["edges"]])
-                        if key in seen:
-                            continue
-                        seen.add(key)
-                        d["attempt"] = att
-                        d["kind"] = kind
-                        got.append(d)
-                        print("keep", kind, q, att, d["sample_matches"], flush=True)
-                    elif d is not None:
-                        out["rejected"].append({"kind": kind, "q": q, "attempt": att, "why": why})
-                next_attempt[(kind, q)] = attempt
-                save_partial()
-            carry[kind] = need - len(got)
-            if carry[kind]:
-                print("short", kind, q, carry[kind], flush=True)
-            if carry[kind] and q == qmin[kind]:
-                raise SystemExit("could not find %d %s queries of %d vertices" % (carry[kind], kind, q))
-    # assign to the plan's slots: a size's own slots first, then those that fell from above
-    avail = {c: list(v) for c, v in chosen.items()}
-    slot_of = {}
-    for kind in kinds:
-        falling = []
-        for q in range(qmax[kind], qmin[kind] - 1, -1):
-            planned = [q] * want.get((kind, q), 0) + falling
-            take = avail[(kind, q)]
-            for j, pq in enumerate(planned[:len(take)]):
-                d = dict(take[j])
-                d["q_planned"] = pq
-                slot_of.setdefault((kind, pq), []).append(d)
-            falling = planned[len(take):]
+                print("%s %d: attempts %d, kept %d, rejected %s [%.0fs]" % (kind, q, attempt - len(jobs), len(got),
+                                                                         json.dumps(rej), time.time() - t0), flush=True)
+                for att, d, why in pool.imap(_try, jobs):
+                    if why is not None:
+                        rej[why] = rej.get(why, 0) + 1
+                        continue
+                    key = json.dumps([d["labels"], d["edges"]])
+                    if key in seen or len(got) >= need:
+                        continue
+                    seen.add(key)
+                    got.append(d)
+                    print("keep %s %d attempt %d: sample %d heavy %d (%.1fs) [%.0fs]" % (
+                        kind, q, att, d["sample_matches"], d["heavy_matches"], d["check_seconds"],
+                        time.time() - t0), flush=True)
+            rej["attempts"] = attempt
+            if len(got) < need:
+                raise SystemExit("found only %d of %d %s queries of %d vertices in %d attempts" % (
+                    len(got), need, kind, q, attempt))
+    if args.kind is not None:  # one class: a partial file, merged later
+        out["chosen"] = {"%s:%d" % k: v for k, v in chosen.items()}
+        path = os.path.join(HERE, "queries_%s.%s.partial" % (args.name, args.kind))
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+        print("wrote", path, "in %.0f s" % (time.time() - t0))
+        return
     used = {}
-    for kind, q in plan:
+    for kind, q in spec["plan"]:
         i = used.get((kind, q), 0)
-        out["queries"].append(slot_of[(kind, q)][i])
+        out["queries"].append(chosen[(kind, q)][i])
         used[(kind, q)] = i + 1
+    path = os.path.join(HERE, "queries_%s.json" % args.name)
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
-    if os.path.exists(partial):
-        os.remove(partial)
-    print("wrote", path, len(out["queries"]), "queries,", len(out["rejected"]), "rejected")
+    print("wrote", path, len(out["queries"]), "queries in %.0f s" % (time.time() - t0))
+
+
+def merge(name):
+    """Assemble queries_NAME.json from the per-class partial files."""
+    spec = SPECS[name]
+    chosen, rejected, head = {}, {}, None
+    for kind in sorted({k for k, _ in spec["plan"]}):
+        with open(os.path.join(HERE, "queries_%s.%s.partial" % (name, kind))) as f:
+            d = json.load(f)
+        head = head or d
+        rejected.update(d["rejected"])
+        for key, v in d["chosen"].items():
+            k, q = key.split(":")
+            chosen[(k, int(q))] = v
+    out = {k: head[k] for k in ("workload", "graph_digest", "selection_batch_updates", "rule")}
+    out["queries"], out["rejected"] = [], rejected
+    used = {}
+    for kind, q in spec["plan"]:
+        i = used.get((kind, q), 0)
+        out["queries"].append(chosen[(kind, q)][i])
+        used[(kind, q)] = i + 1
+    path = os.path.join(HERE, "queries_%s.json" % name)
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print("wrote", path, len(out["queries"]), "queries")
 
 
 if __name__ == "__main__":
