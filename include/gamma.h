@@ -132,6 +132,17 @@ GAMMA_API void gamma_destroy(gamma_ctx *ctx);
 GAMMA_API int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels,
                      int64_t m, const int32_t *src, const int32_t *dst);
 
+/* Edge-labelled graph (Sec. II-A: the label function covers edges too; the
+ * paper's NF and LS datasets, Table II, have edge labels): as
+ * gamma_load_graph, with elabels[m] the label of edge e in [0, 255] (host or
+ * device).  A repeated edge must repeat its label (else GAMMA_EINVAL).  An
+ * embedding must then map every query edge onto a data edge of the query
+ * edge's label.  With elabels NULL this is gamma_load_graph (every edge label
+ * 0).  Limits: gamma_apply_batches (several requests) and gamma_checkpoint
+ * refuse an edge-labelled graph (GAMMA_EINVAL). */
+GAMMA_API int gamma_load_graph_el(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m, const int32_t *src,
+                                  const int32_t *dst, const int32_t *elabels);
+
 /* Register a query graph Q (Sec. II-A): 2 <= q <= 16 vertices with
  * qlabels[q], eq undirected edges (qsrc[e], qdst[e]) in [0, q).  Q must be
  * connected and simple.  The host builds one matching order per query edge
@@ -139,6 +150,13 @@ GAMMA_API int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels,
 GAMMA_API int gamma_register_query(gamma_ctx *ctx, int32_t q, const int32_t *qlabels,
                          int32_t eq, const int32_t *qsrc, const int32_t *qdst,
                          int32_t *out_qid);
+
+/* As gamma_register_query, with qelabels[eq] the label in [0, 255] of each
+ * query edge (host array; NULL: all 0).  On a graph without edge labels a
+ * query edge labelled other than 0 has no image, so the query never matches. */
+GAMMA_API int gamma_register_query_el(gamma_ctx *ctx, int32_t q, const int32_t *qlabels, int32_t eq,
+                                      const int32_t *qsrc, const int32_t *qdst, const int32_t *qelabels,
+                                      int32_t *out_qid);
 
 /* Apply one update batch Delta-B (Def. 1) of b updates: op[k] = +1 inserts
  * edge (src[k], dst[k]), -1 deletes it; the position k is the update's index
@@ -156,6 +174,15 @@ GAMMA_API int gamma_apply_batch(gamma_ctx *ctx, int64_t b, const int8_t *op,
                       int32_t nq, const int32_t *qids,
                       uint64_t *out_pos, uint64_t *out_neg,
                       gamma_matches *opt_out);
+
+/* As gamma_apply_batch on an edge-labelled graph (gamma_load_graph_el):
+ * elab[k] in [0, 255] is the label of the edge update k inserts (ignored for
+ * a deletion, which removes the edge whatever its label; a label outside the
+ * range makes update k invalid).  elab NULL: every insertion gets label 0.
+ * GAMMA_EINVAL with elab on a graph loaded without edge labels. */
+GAMMA_API int gamma_apply_batch_el(gamma_ctx *ctx, int64_t b, const int8_t *op, const int32_t *src,
+                                   const int32_t *dst, const int32_t *elab, int32_t nq, const int32_t *qids,
+                                   uint64_t *out_pos, uint64_t *out_neg, gamma_matches *opt_out);
 
 /* Several update requests staged as one batch (continuous batching): request
  * r is updates [req_off[r], req_off[r+1]) of the arrays (req_off[0] = 0,

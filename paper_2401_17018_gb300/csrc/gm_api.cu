@@ -30,6 +30,7 @@ struct HostQuery {
   int q = 0;
   std::vector<int32_t> lab;
   std::vector<std::pair<int, int>> edges;
+  std::vector<int32_t> elab;  // label of each edge (0 without edge labels)
   std::vector<Plan> plans;
   bool never = false;  // a label absent from G: no embedding can exist
 };
@@ -77,6 +78,7 @@ struct gamma_ctx {
   int32_t *d_label = nullptr;
   uint2 *d_adj = nullptr;
   uint32_t *d_cap = nullptr, *d_col = nullptr, *d_etag = nullptr;
+  uint8_t *d_elab = nullptr;  // edge label per adjacency entry (edge-labelled graphs only)
   uint8_t *d_nlf = nullptr;
   int32_t *d_vgroup = nullptr;
   int32_t *d_hub_id = nullptr;
@@ -98,7 +100,7 @@ struct gamma_ctx {
   StageBufs sb;
   int64_t in_cap = 0;
   int8_t *d_in_op = nullptr;
-  int32_t *d_in_src = nullptr, *d_in_dst = nullptr;
+  int32_t *d_in_src = nullptr, *d_in_dst = nullptr, *d_in_elab = nullptr;
   bool staged = false;
   int64_t b = 0;
   std::vector<int32_t> qids;
@@ -146,6 +148,7 @@ struct gamma_ctx {
   GraphDev gd() const {
     GraphDev g;
     g.label = d_label; g.adj = d_adj; g.cap = d_cap; g.col = d_col; g.etag = d_etag; g.nlf = d_nlf;
+    g.elab = d_elab;
     g.vgroup = d_vgroup;
     g.hub_id = d_hub_id; g.hub_lofs = d_hub_lofs; g.hub_tab = d_hub_tab; g.hub_keys = d_hub_keys;
     g.hub_keys_cap = hub_keys_cap; g.nhub = nhub;
@@ -204,7 +207,8 @@ int grow_vertex_array(gamma_ctx *ctx, T **arr, size_t per, int32_t n, int32_t n2
 void free_graph(gamma_ctx *ctx) {
   drop_graph_exec(ctx);
   cudaFree(ctx->d_label); cudaFree(ctx->d_adj); cudaFree(ctx->d_cap);
-  cudaFree(ctx->d_col); cudaFree(ctx->d_etag); cudaFree(ctx->d_nlf);
+  cudaFree(ctx->d_col); cudaFree(ctx->d_etag); cudaFree(ctx->d_nlf); cudaFree(ctx->d_elab);
+  ctx->d_elab = nullptr;
   cudaFree(ctx->d_hub_id); cudaFree(ctx->d_hub_lofs); cudaFree(ctx->d_hub_tab); cudaFree(ctx->d_hub_keys);
   cudaFree(ctx->d_vgroup);
   ctx->d_vgroup = nullptr;
@@ -229,8 +233,14 @@ int bits_for(int64_t x) {  // bits to represent values 0..x-1 (>= 1)
 void make_plan(const HostQuery &Q, int qid, int a, int b, const std::vector<int64_t> &freq, Plan &P) {
   const int q = Q.q;
   std::vector<std::vector<char>> adjq(q, std::vector<char>(q, 0));
+  std::vector<std::vector<int>> elq(q, std::vector<int>(q, 0));  // query edge labels
   std::vector<int> deg(q, 0);
-  for (auto &e : Q.edges) { adjq[e.first][e.second] = adjq[e.second][e.first] = 1; deg[e.first]++; deg[e.second]++; }
+  for (size_t i = 0; i < Q.edges.size(); i++) {
+    const auto &e = Q.edges[i];
+    adjq[e.first][e.second] = adjq[e.second][e.first] = 1;
+    deg[e.first]++; deg[e.second]++;
+    elq[e.first][e.second] = elq[e.second][e.first] = i < Q.elab.size() ? Q.elab[i] : 0;
+  }
   std::vector<int> order = {a, b};
   std::vector<char> placed(q, 0);
   placed[a] = placed[b] = 1;
@@ -262,6 +272,7 @@ void make_plan(const HostQuery &Q, int qid, int a, int b, const std::vector<int6
     uint16_t bw = 0, sl = 0;
     for (int k = 0; k < l; k++) {
       if (adjq[u][order[k]]) bw |= (uint16_t)(1u << k);
+      P.el[l][k] = (uint8_t)elq[u][order[k]];
       if (Q.lab[order[k]] == Q.lab[u]) sl |= (uint16_t)(1u << k);
     }
     P.bwd[l] = bw;
@@ -346,15 +357,20 @@ int grow_pool(gamma_ctx *ctx, uint64_t need) {
   if (cap >= (1ull << 32) - 64) cap = (1ull << 32) - 64;
   if (cap <= ctx->pool_cap) return ctx->fail(GAMMA_ENOMEM, "adjacency pool cannot grow past 2^32 slots");
   uint32_t *col = nullptr, *etag = nullptr;
+  uint8_t *elab = nullptr;
   CKC(cudaMalloc((void **)&col, sizeof(uint32_t) * (cap + GM_COL_PAD)));  // padded: short lists are read in 16-byte words
   CKC(cudaMalloc((void **)&etag, sizeof(uint32_t) * cap));
+  if (ctx->d_elab) CKC(cudaMalloc((void **)&elab, cap + GM_COL_PAD));
   CKC(cudaMemcpyAsync(col, ctx->d_col, sizeof(uint32_t) * ctx->pool_top, cudaMemcpyDeviceToDevice, ctx->stream));
   CKC(cudaMemcpyAsync(etag, ctx->d_etag, sizeof(uint32_t) * ctx->pool_top, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (elab) CKC(cudaMemcpyAsync(elab, ctx->d_elab, ctx->pool_top, cudaMemcpyDeviceToDevice, ctx->stream));
   CKC(cudaStreamSynchronize(ctx->stream));
   cudaFree(ctx->d_col);
   cudaFree(ctx->d_etag);
+  cudaFree(ctx->d_elab);
   ctx->d_col = col;
   ctx->d_etag = etag;
+  ctx->d_elab = elab;
   ctx->pool_cap = (uint32_t)cap;
   return GAMMA_OK;
 }
@@ -379,7 +395,7 @@ int prepare_buffers(gamma_ctx *ctx, int64_t b) {
   if (b > sb.cap) {
     int64_t c = std::max<int64_t>(b, 1024);
     void *ps[] = {sb.cu, sb.cv, sb.cop, sb.keys, sb.tk, sb.vals, sb.tv, sb.head, sb.gid, sb.gv, sb.gstart,
-                  sb.gins, sb.greloc, sb.bkeys, sb.cnext, sb.cinfo};
+                  sb.gins, sb.greloc, sb.bkeys, sb.cnext, sb.cinfo, sb.ulab};
     for (void *p : ps) if (p) cudaFree(p);
     sb = StageBufs();
     CKC(cudaMalloc((void **)&sb.cu, 4 * c)); CKC(cudaMalloc((void **)&sb.cv, 4 * c));
@@ -392,15 +408,17 @@ int prepare_buffers(gamma_ctx *ctx, int64_t b) {
     CKC(cudaMalloc((void **)&sb.bkeys, 8 * c));
     CKC(cudaMalloc((void **)&sb.cnext, 4 * c));
     CKC(cudaMalloc((void **)&sb.cinfo, c));
+    CKC(cudaMalloc((void **)&sb.ulab, c));
     sb.cap = c;
   }
   if (b > ctx->in_cap) {
-    cudaFree(ctx->d_in_op); cudaFree(ctx->d_in_src); cudaFree(ctx->d_in_dst);
-    ctx->d_in_op = nullptr; ctx->d_in_src = nullptr; ctx->d_in_dst = nullptr;
+    cudaFree(ctx->d_in_op); cudaFree(ctx->d_in_src); cudaFree(ctx->d_in_dst); cudaFree(ctx->d_in_elab);
+    ctx->d_in_op = nullptr; ctx->d_in_src = nullptr; ctx->d_in_dst = nullptr; ctx->d_in_elab = nullptr;
     int64_t c = std::max<int64_t>(b, 1024);
     CKC(cudaMalloc((void **)&ctx->d_in_op, c));
     CKC(cudaMalloc((void **)&ctx->d_in_src, 4 * c));
     CKC(cudaMalloc((void **)&ctx->d_in_dst, 4 * c));
+    CKC(cudaMalloc((void **)&ctx->d_in_elab, 4 * c));
     ctx->in_cap = c;
   }
   const int nq = (int)ctx->qids.size();
@@ -423,12 +441,13 @@ int prepare_buffers(gamma_ctx *ctx, int64_t b) {
 }
 
 // status reset + stage; no host sync
-int enqueue_stage(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const int32_t *ddst) {
+int enqueue_stage(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const int32_t *ddst, const int32_t *delab) {
   cudaStream_t s = ctx->stream;
   CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st_init, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
   CKC(cudaEventRecord(ctx->ev[0], s));
   if (ctx->b > 0)
-    CK(gm_stage(ctx->gd(), dop, dsrc, ddst, ctx->b, ctx->nreq > 1 ? ctx->d_req : nullptr, ctx->sb, ctx->d_st, s));
+    CK(gm_stage(ctx->gd(), dop, dsrc, ddst, delab, ctx->b, ctx->nreq > 1 ? ctx->d_req : nullptr, ctx->sb, ctx->d_st,
+                s));
   CKC(cudaEventRecord(ctx->ev[1], s));
   return GAMMA_OK;
 }
@@ -453,6 +472,7 @@ int enqueue_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_s
   MatchArgs a;
   a.g = ctx->gd();
   a.cu = ctx->sb.cu; a.cv = ctx->sb.cv; a.op = ctx->sb.cop; a.b = b;
+  a.ulab = ctx->d_elab ? ctx->sb.ulab : nullptr;
   a.grain = ctx->grain;
   a.items = ctx->d_items; a.item_cap = (uint64_t)ctx->items_cap;
   a.cnt = ctx->d_cnt;
@@ -466,7 +486,9 @@ int enqueue_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_s
   a.tile = ctx->tile;
   a.warps_per_block = ctx->wpb;
   a.count_bytes = (ctx->flags & GAMMA_F_COUNT_BYTES) ? 1 : 0;
-  a.leaf = (ctx->flags & GAMMA_F_NO_LEAF) ? 0 : 1;
+  // the closed-form count of a last vertex assumes every slot of its driver
+  // slice is an edge it may use; edge labels break that, so it is off then
+  a.leaf = ((ctx->flags & GAMMA_F_NO_LEAF) || ctx->d_elab) ? 0 : 1;
   a.share = (rows_dev == nullptr && !(ctx->flags & GAMMA_F_NO_SHARE)) ? 1 : 0;
   a.bkeys = ctx->sb.keys;
   a.bvals = ctx->sb.vals;
@@ -574,8 +596,8 @@ int match_with_rows(gamma_ctx *ctx, gamma_matches *out) {
 
 // stage + match in one stream sequence (optionally replayed as a CUDA graph),
 // one host sync; retried after growing the adjacency pool or the item buffer
-int run_apply(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const int32_t *ddst, int32_t *rows,
-              uint64_t row_cap, int row_stride) {
+int run_apply(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const int32_t *ddst, const int32_t *delab,
+              int32_t *rows, uint64_t row_cap, int row_stride) {
   cudaStream_t s = ctx->stream;
   for (int attempt = 0; attempt < 4; attempt++) {
     CK(prepare_buffers(ctx, ctx->b));
@@ -589,12 +611,13 @@ int run_apply(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const int3
                                   (int64_t)(intptr_t)ctx->d_pair_off, (int64_t)(intptr_t)ctx->d_pair_plans,
                                   (int64_t)(intptr_t)ctx->sb.cu, (int64_t)(intptr_t)ctx->d_cnt,
                                   (int64_t)(intptr_t)ctx->d_per_upd, (int64_t)(intptr_t)ctx->d_req,
-                                  (int64_t)(intptr_t)ctx->h_cnt, ctx->nplans, ctx->maxq};
+                                  (int64_t)(intptr_t)ctx->h_cnt, ctx->nplans, ctx->maxq, (int64_t)(intptr_t)delab,
+                                  (int64_t)(intptr_t)ctx->d_elab, (int64_t)(intptr_t)ctx->sb.ulab};
       key.insert(key.end(), ctx->plan_key.begin(), ctx->plan_key.end());
       if (key != ctx->gkey || !ctx->gexec) {
         cudaGraph_t graph = nullptr;
         CKC(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-        int rc1 = enqueue_stage(ctx, dop, dsrc, ddst);
+        int rc1 = enqueue_stage(ctx, dop, dsrc, ddst, delab);
         int rc2 = rc1 ? rc1 : enqueue_match(ctx, rows, row_cap, row_stride, false);
         cudaError_t ce = cudaStreamEndCapture(s, &graph);
         if (rc2) { if (graph) cudaGraphDestroy(graph); return ctx->cuda_fail(rc2); }
@@ -608,7 +631,7 @@ int run_apply(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const int3
       }
       CKC(cudaGraphLaunch(ctx->gexec, s));
     } else {
-      CK(enqueue_stage(ctx, dop, dsrc, ddst));
+      CK(enqueue_stage(ctx, dop, dsrc, ddst, delab));
       CK(enqueue_match(ctx, rows, row_cap, row_stride, false));
     }
     CKC(cudaStreamSynchronize(s));
@@ -638,8 +661,8 @@ int run_apply(gamma_ctx *ctx, const int8_t *dop, const int32_t *dsrc, const int3
 }
 
 int apply_impl(gamma_ctx *ctx, const char *fn, int32_t nreq, const int64_t *req_off, int64_t b, const int8_t *op,
-               const int32_t *src, const int32_t *dst, int32_t nq, const int32_t *qids, uint64_t *out_pos,
-               uint64_t *out_neg, gamma_matches *opt_out) {
+               const int32_t *src, const int32_t *dst, const int32_t *elab, int32_t nq, const int32_t *qids,
+               uint64_t *out_pos, uint64_t *out_neg, gamma_matches *opt_out) {
   if (!ctx) return GAMMA_EINVAL;
   ctx->err.clear();
   if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "%s: no graph loaded", fn);
@@ -650,6 +673,10 @@ int apply_impl(gamma_ctx *ctx, const char *fn, int32_t nreq, const int64_t *req_
   for (int j = 0; j < nq; j++)
     if (qids[j] < 0 || qids[j] >= (int)ctx->queries.size())
       return ctx->fail(GAMMA_EINVAL, "%s: unknown query id %d", fn, qids[j]);
+  if (elab && !ctx->d_elab)
+    return ctx->fail(GAMMA_EINVAL, "%s: edge labels need a graph loaded with gamma_load_graph_el", fn);
+  if (nreq > 1 && ctx->d_elab)
+    return ctx->fail(GAMMA_EINVAL, "%s: requests staged together need a graph without edge labels", fn);
   cudaSetDevice(ctx->device);
   cudaStream_t s = ctx->stream;
   ctx->b = b;
@@ -669,7 +696,7 @@ int apply_impl(gamma_ctx *ctx, const char *fn, int32_t nreq, const int64_t *req_
     CKC(cudaStreamSynchronize(s));
   }
   const int8_t *dop = op;
-  const int32_t *dsrc = src, *ddst = dst;
+  const int32_t *dsrc = src, *ddst = dst, *delab = nullptr;
   if (b > 0) {
     bool dev = is_device_ptr(op) && is_device_ptr(src) && is_device_ptr(dst);
     if (!dev || (ctx->flags & GAMMA_F_GRAPH)) {  // the graph reads fixed staging buffers
@@ -678,12 +705,17 @@ int apply_impl(gamma_ctx *ctx, const char *fn, int32_t nreq, const int64_t *req_
       CKC(cudaMemcpyAsync(ctx->d_in_dst, dst, 4 * b, cudaMemcpyDefault, s));
       dop = ctx->d_in_op; dsrc = ctx->d_in_src; ddst = ctx->d_in_dst;
     }
+    if (elab) {  // insertion labels, always through the context's buffer
+      CKC(cudaMemcpyAsync(ctx->d_in_elab, elab, 4 * b, cudaMemcpyDefault, s));
+      delab = ctx->d_in_elab;
+    }
   }
   int32_t *rows;
   bool devrows;
   rc = rows_target(ctx, opt_out, &rows, &devrows);
   if (rc) return rc;
-  rc = run_apply(ctx, dop, dsrc, ddst, rows, opt_out ? (uint64_t)opt_out->capacity : 0, opt_out ? opt_out->stride : 0);
+  rc = run_apply(ctx, dop, dsrc, ddst, delab, rows, opt_out ? (uint64_t)opt_out->capacity : 0,
+                 opt_out ? opt_out->stride : 0);
   if (rc) return ctx->err.empty() ? ctx->fail(rc, "%s failed", fn) : rc;
   GmStatus st = *ctx->h_st;
   if (!ctx->staged) {
@@ -772,7 +804,7 @@ void gamma_destroy(gamma_ctx *ctx) {
   free_graph(ctx);
   StageBufs &sb = ctx->sb;
   void *ps[] = {sb.cu, sb.cv, sb.cop, sb.keys, sb.tk, sb.vals, sb.tv, sb.head, sb.gid, sb.gv, sb.gstart,
-                sb.gins, sb.greloc, sb.bkeys, sb.cnext, sb.cinfo, ctx->d_in_op, ctx->d_in_src, ctx->d_in_dst, ctx->d_plans,
+                sb.gins, sb.greloc, sb.bkeys, sb.cnext, sb.cinfo, sb.ulab, ctx->d_in_elab, ctx->d_in_op, ctx->d_in_src, ctx->d_in_dst, ctx->d_plans,
                 ctx->d_pair_off, ctx->d_pair_plans, ctx->d_items, ctx->d_cnt, ctx->d_per_upd, ctx->d_rows,
                 ctx->d_tasks, ctx->d_task_seq, ctx->d_sched, ctx->d_req, ctx->d_st};
   for (void *p : ps) if (p) cudaFree(p);
@@ -809,6 +841,7 @@ int gm_recount_prepare(gamma_ctx *ctx, MatchArgs *a, int *nslots, int *num_sms, 
   MatchArgs &m = *a;
   m.g = ctx->gd();
   m.cu = ctx->sb.cu; m.cv = ctx->sb.cv; m.op = ctx->sb.cop; m.b = ctx->b;
+  m.ulab = ctx->d_elab ? ctx->sb.ulab : nullptr;
   m.plans = ctx->d_plans; m.nplans = ctx->nplans;
   m.pair_off = ctx->d_pair_off; m.pair_plans = ctx->d_pair_plans;
   m.grain = ctx->grain;
@@ -825,7 +858,7 @@ int gm_recount_prepare(gamma_ctx *ctx, MatchArgs *a, int *nslots, int *num_sms, 
   m.nlev = std::max(1, ctx->maxq - 3);
   m.warps_per_block = ctx->wpb;
   m.count_bytes = 0;
-  m.leaf = (ctx->flags & GAMMA_F_NO_LEAF) ? 0 : 1;
+  m.leaf = ((ctx->flags & GAMMA_F_NO_LEAF) || ctx->d_elab) ? 0 : 1;
   m.share = (ctx->flags & GAMMA_F_NO_SHARE) ? 0 : 1;
   m.bkeys = ctx->sb.keys; m.bvals = ctx->sb.vals; m.gstart = ctx->sb.gstart; m.gins = ctx->sb.gins;
   m.n2 = (uint32_t)(2 * ctx->b);
@@ -866,6 +899,11 @@ int gamma_set_options(gamma_ctx *ctx, const gamma_options *o) {
 
 int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m, const int32_t *src,
                      const int32_t *dst) {
+  return gamma_load_graph_el(ctx, n, labels, m, src, dst, nullptr);
+}
+
+int gamma_load_graph_el(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m, const int32_t *src,
+                        const int32_t *dst, const int32_t *elabels) {
   if (!ctx) return GAMMA_EINVAL;
   ctx->err.clear();
   if (n <= 0 || m < 0 || !labels || (m > 0 && (!src || !dst)))
@@ -877,8 +915,8 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
   ctx->plan_key.clear();
   cudaStream_t s = ctx->stream;
   // device copies of the inputs
-  const int32_t *dl = labels, *ds = src, *dd = dst;
-  int32_t *ts = nullptr, *td = nullptr;
+  const int32_t *dl = labels, *ds = src, *dd = dst, *de = elabels;
+  int32_t *ts = nullptr, *td = nullptr, *te = nullptr;
   CKC(cudaMalloc((void **)&ctx->d_label, sizeof(int32_t) * n));
   CKC(cudaMemcpyAsync(ctx->d_label, labels, sizeof(int32_t) * n, cudaMemcpyDefault, s));
   dl = ctx->d_label;
@@ -892,21 +930,26 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
     CKC(cudaMemcpyAsync(td, dst, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
     dd = td;
   }
+  if (elabels && !is_device_ptr(elabels)) {
+    CKC(cudaMalloc((void **)&te, sizeof(int32_t) * std::max<int64_t>(m, 1)));
+    if (m > 0) CKC(cudaMemcpyAsync(te, elabels, sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    de = te;
+  }
   reset_status_host(ctx);
   CKC(cudaMemcpyAsync(ctx->d_st, ctx->h_st_init, sizeof(GmStatus), cudaMemcpyHostToDevice, s));
-  CK(gm_load_validate(dl, n, ds, dd, m, ctx->d_st, s));
+  CK(gm_load_validate(dl, n, ds, dd, de, m, ctx->d_st, s));
   CKC(cudaMemcpyAsync(ctx->h_st, ctx->d_st, sizeof(GmStatus), cudaMemcpyDeviceToHost, s));
   CKC(cudaStreamSynchronize(s));
   if (ctx->h_st->err) {
-    cudaFree(ts); cudaFree(td);
+    cudaFree(ts); cudaFree(td); cudaFree(te);
     free_graph(ctx);
     if (ctx->h_st->bad_index != INT64_MAX)
-      return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: edge %lld has an id out of range or is a self-loop",
-                       (long long)ctx->h_st->bad_index);
+      return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: edge %lld has an id out of range, is a self-loop or has a "
+                       "label outside [0, 255]", (long long)ctx->h_st->bad_index);
     return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: negative vertex label");
   }
   if (ctx->h_st->max_label > 255) {
-    cudaFree(ts); cudaFree(td);
+    cudaFree(ts); cudaFree(td); cudaFree(te);
     free_graph(ctx);
     return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: vertex labels must be < 256");
   }
@@ -916,7 +959,7 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
   ctx->idb = bits_for(ctx->n_cap);
   int lb = bits_for(ctx->nlab);
   if (1 + ctx->idb + lb > 32) {
-    cudaFree(ts); cudaFree(td);
+    cudaFree(ts); cudaFree(td); cudaFree(te);
     free_graph(ctx);
     return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: %d vertex-id bits + %d label bits + 1 exceed 32", ctx->idb, lb);
   }
@@ -929,8 +972,14 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
   CKC(cudaMemsetAsync(ctx->d_nlf, 0, (size_t)n * ctx->nlfw, s));
   uint32_t pool_cap = 0;
   GraphDev g = ctx->gd();
-  CK(gm_load_build(g, ds, dd, m, &ctx->d_col, &ctx->d_etag, &pool_cap, 1.25, (uint64_t)1 << 20, ctx->d_st,
-                   ctx->h_st, s));
+  CK(gm_load_build(g, ds, dd, de, m, &ctx->d_col, &ctx->d_etag, &ctx->d_elab, &pool_cap, 1.25, (uint64_t)1 << 20,
+                   ctx->d_st, ctx->h_st, s));
+  if (ctx->h_st->err) {  // a repeated edge whose copies carry different labels
+    CKC(cudaStreamSynchronize(s));
+    cudaFree(ts); cudaFree(td); cudaFree(te);
+    free_graph(ctx);
+    return ctx->fail(GAMMA_EINVAL, "gamma_load_graph: an edge is listed twice with different labels");
+  }
   ctx->pool_cap = pool_cap;
   ctx->pool_top = ctx->h_st->pool_top;
   g = ctx->gd();
@@ -942,6 +991,7 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
   CKC(cudaStreamSynchronize(s));
   cudaFree(ts);
   cudaFree(td);
+  cudaFree(te);
   ctx->label_freq.assign(ctx->nlab, 0);
   for (int32_t v = 0; v < n; v++) ctx->label_freq[hl[v]]++;
   // live directed entries = sum of list lengths
@@ -997,6 +1047,11 @@ int gamma_load_graph(gamma_ctx *ctx, int32_t n, const int32_t *labels, int64_t m
 
 int gamma_register_query(gamma_ctx *ctx, int32_t q, const int32_t *qlabels, int32_t eq, const int32_t *qsrc,
                          const int32_t *qdst, int32_t *out_qid) {
+  return gamma_register_query_el(ctx, q, qlabels, eq, qsrc, qdst, nullptr, out_qid);
+}
+
+int gamma_register_query_el(gamma_ctx *ctx, int32_t q, const int32_t *qlabels, int32_t eq, const int32_t *qsrc,
+                            const int32_t *qdst, const int32_t *qelabels, int32_t *out_qid) {
   if (!ctx) return GAMMA_EINVAL;
   ctx->err.clear();
   if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "gamma_register_query: no graph loaded");
@@ -1012,6 +1067,10 @@ int gamma_register_query(gamma_ctx *ctx, int32_t q, const int32_t *qlabels, int3
       return ctx->fail(GAMMA_EINVAL, "gamma_register_query: edge %d is out of range, a self-loop or repeated", e);
     adjq[a][b] = adjq[b][a] = 1;
     Q.edges.push_back({a, b});
+    const int32_t el = qelabels ? qelabels[e] : 0;
+    if (el < 0 || el > 255) return ctx->fail(GAMMA_EINVAL, "gamma_register_query: edge label outside [0, 255]");
+    Q.elab.push_back(el);
+    if (el != 0 && !ctx->d_elab) Q.never = true;  // every edge of an unlabelled graph has label 0
   }
   for (int u = 0; u < q; u++) {
     if (Q.lab[u] < 0) return ctx->fail(GAMMA_EINVAL, "gamma_register_query: negative label");
@@ -1046,7 +1105,14 @@ int gamma_apply_batch(gamma_ctx *ctx, int64_t b, const int8_t *op, const int32_t
                       int32_t nq, const int32_t *qids, uint64_t *out_pos, uint64_t *out_neg,
                       gamma_matches *opt_out) {
   const int64_t off[2] = {0, b};
-  return apply_impl(ctx, "gamma_apply_batch", 1, off, b, op, src, dst, nq, qids, out_pos, out_neg, opt_out);
+  return apply_impl(ctx, "gamma_apply_batch", 1, off, b, op, src, dst, nullptr, nq, qids, out_pos, out_neg, opt_out);
+}
+
+int gamma_apply_batch_el(gamma_ctx *ctx, int64_t b, const int8_t *op, const int32_t *src, const int32_t *dst,
+                         const int32_t *elab, int32_t nq, const int32_t *qids, uint64_t *out_pos, uint64_t *out_neg,
+                         gamma_matches *opt_out) {
+  const int64_t off[2] = {0, b};
+  return apply_impl(ctx, "gamma_apply_batch_el", 1, off, b, op, src, dst, elab, nq, qids, out_pos, out_neg, opt_out);
 }
 
 int gamma_apply_batches(gamma_ctx *ctx, int32_t nreq, const int64_t *req_off, const int8_t *op,
@@ -1054,8 +1120,8 @@ int gamma_apply_batches(gamma_ctx *ctx, int32_t nreq, const int64_t *req_off, co
                         uint64_t *out_pos, uint64_t *out_neg) {
   if (!ctx) return GAMMA_EINVAL;
   if (nreq < 1 || !req_off) return ctx->fail(GAMMA_EINVAL, "gamma_apply_batches: need nreq >= 1 and offsets");
-  return apply_impl(ctx, "gamma_apply_batches", nreq, req_off, req_off[nreq], op, src, dst, nq, qids, out_pos,
-                    out_neg, nullptr);
+  return apply_impl(ctx, "gamma_apply_batches", nreq, req_off, req_off[nreq], op, src, dst, nullptr, nq, qids,
+                    out_pos, out_neg, nullptr);
 }
 
 int gamma_fetch_matches(gamma_ctx *ctx, gamma_matches *out) {
@@ -1245,6 +1311,7 @@ int gamma_checkpoint(gamma_ctx *ctx, void *buf, int64_t cap, int64_t *size) {
   ctx->err.clear();
   if (!ctx->loaded) return ctx->fail(GAMMA_ESTATE, "gamma_checkpoint: no graph loaded");
   if (ctx->staged) return ctx->fail(GAMMA_ESTATE, "gamma_checkpoint: a batch is staged; commit it first");
+  if (ctx->d_elab) return ctx->fail(GAMMA_EINVAL, "gamma_checkpoint: edge labels are not checkpointed");
   if (!size || (cap > 0 && !buf)) return ctx->fail(GAMMA_EINVAL, "gamma_checkpoint: null output");
   cudaSetDevice(ctx->device);
   CKC(cudaStreamSynchronize(ctx->stream));

@@ -62,6 +62,7 @@ struct GraphDev {
   uint32_t *cap;         // [n] slots reserved at offset
   uint32_t *col;         // [pool] adjacency keys
   uint32_t *etag;        // [pool] batch tag of flagged entries
+  uint8_t *elab;         // [pool] edge label of each entry (null: an unlabelled graph, every edge label 0)
   uint8_t *nlf;          // [n * nlfw] per-label neighbour counts of the union graph, saturated at 255
   int32_t *vgroup;       // [n] while a batch is staged: the vertex's group in the sorted batch, else -1
   // hub index: vertices whose list had >= the hub threshold entries at load keep the
@@ -95,6 +96,7 @@ struct Plan {
   uint8_t nreq[GM_MAXQ];          // neighbour-label requirements of pi[l]
   uint8_t req_lab[GM_MAXQ][GM_MAXQ - 1];
   uint8_t req_cnt[GM_MAXQ][GM_MAXQ - 1];
+  uint8_t el[GM_MAXQ][GM_MAXQ];   // el[l][k], k < l: label of the query edge (pi[l], pi[k]) (Sec. II-A)
 };
 
 // DFS work item: a seed (update, plan) and a slice of its level-2 candidates

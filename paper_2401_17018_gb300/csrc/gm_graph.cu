@@ -32,7 +32,7 @@ __device__ __forceinline__ uint32_t slack_cap(uint32_t len) {
 // ------------------------------- load ---------------------------------------
 __global__ void k_load_validate(const int32_t *__restrict__ labels, int32_t n,
                                 const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
-                                int64_t m, GmStatus *st) {
+                                const int32_t *__restrict__ elabels, int64_t m, GmStatus *st) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n || i < m; i += stride) {
     if (i < n) {
@@ -42,7 +42,8 @@ __global__ void k_load_validate(const int32_t *__restrict__ labels, int32_t n,
     }
     if (i < m) {
       int32_t s = src[i], d = dst[i];
-      if (s < 0 || s >= n || d < 0 || d >= n || s == d) {
+      const bool bad_label = elabels && (elabels[i] < 0 || elabels[i] > 255);
+      if (s < 0 || s >= n || d < 0 || d >= n || s == d || bad_label) {
         gm_set_err(st, GAMMA_EINVAL);
         gm_bad_index(st, i);
       }
@@ -50,22 +51,27 @@ __global__ void k_load_validate(const int32_t *__restrict__ labels, int32_t n,
   }
 }
 
-__global__ void k_load_keys(const int32_t *__restrict__ src, const int32_t *__restrict__ dst, int64_t m,
-                            const int32_t *__restrict__ label, int idb, uint64_t *__restrict__ keys) {
+// vals (edge-labelled graphs, else null): each directed entry carries its edge's label through the sort
+__global__ void k_load_keys(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                            const int32_t *__restrict__ elabels, int64_t m, const int32_t *__restrict__ label, int idb,
+                            uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
     uint32_t s = (uint32_t)src[e], d = (uint32_t)dst[e];
     keys[2 * e] = ((uint64_t)s << 32) | gm_key(label[d], d, idb);
     keys[2 * e + 1] = ((uint64_t)d << 32) | gm_key(label[s], s, idb);
+    if (vals) vals[2 * e] = vals[2 * e + 1] = (uint32_t)elabels[e];
   }
 }
 
-__global__ void k_load_uniq(const uint64_t *__restrict__ keys, int64_t n2, uint32_t *__restrict__ flag,
-                            uint32_t *__restrict__ deg) {
+// a repeated edge is merged; with edge labels its copies must agree
+__global__ void k_load_uniq(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n2,
+                            uint32_t *__restrict__ flag, uint32_t *__restrict__ deg, GmStatus *st) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
     uint64_t k = keys[i];
     uint32_t f = (i == 0 || keys[i - 1] != k) ? 1u : 0u;
+    if (!f && vals && vals[i - 1] != vals[i]) gm_set_err(st, GAMMA_EINVAL);
     flag[i] = f;
     if (f) atomicAdd(&deg[k >> 32], 1u);
   }
@@ -76,15 +82,18 @@ __global__ void k_load_caps(const uint32_t *__restrict__ deg, int32_t n, uint32_
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) cap[v] = slack_cap(deg[v]);
 }
 
-__global__ void k_load_scatter(const uint64_t *__restrict__ keys, int64_t n2, const uint32_t *__restrict__ flag,
-                               const uint32_t *__restrict__ pos, const uint32_t *__restrict__ rowstart,
-                               const uint32_t *__restrict__ off, uint32_t *__restrict__ col) {
+__global__ void k_load_scatter(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n2,
+                               const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos,
+                               const uint32_t *__restrict__ rowstart, const uint32_t *__restrict__ off,
+                               uint32_t *__restrict__ col, uint8_t *__restrict__ elab) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
     if (!flag[i]) continue;
     uint64_t k = keys[i];
     uint32_t s = (uint32_t)(k >> 32);
-    col[off[s] + pos[i] - rowstart[s]] = (uint32_t)k;
+    const uint32_t slot = off[s] + pos[i] - rowstart[s];
+    col[slot] = (uint32_t)k;
+    if (elab) elab[slot] = (uint8_t)vals[i];
   }
 }
 
@@ -270,12 +279,16 @@ __global__ void k_stage_prep(const int8_t *__restrict__ op, const int32_t *__res
                              const int32_t *__restrict__ dst, int64_t b, GraphDev g,
                              uint32_t *__restrict__ cu, uint32_t *__restrict__ cv, int8_t *__restrict__ cop,
                              uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                             const uint8_t *__restrict__ cinfo, GmStatus *st) {
+                             const uint8_t *__restrict__ cinfo, const int32_t *__restrict__ elab_in,
+                             uint8_t *__restrict__ ulab, GmStatus *st) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b; k += stride) {
     int o = op[k];
     int32_t s = src[k], d = dst[k];
-    bool bad = (o != 1 && o != -1) || s < 0 || s >= g.n || d < 0 || d >= g.n || s == d;
+    // edge-labelled graph: an insertion's label (a deletion's is read while merging)
+    const int32_t el = (g.elab && elab_in && o == 1) ? elab_in[k] : 0;
+    if (g.elab) ulab[k] = (uint8_t)el;
+    bool bad = (o != 1 && o != -1) || s < 0 || s >= g.n || d < 0 || d >= g.n || s == d || el < 0 || el > 255;
     if (bad) {
       gm_set_err(st, GAMMA_EINVAL);
       gm_bad_index(st, k);
@@ -387,7 +400,7 @@ __device__ __forceinline__ uint32_t merge_path(const uint32_t *A, uint32_t na, c
 __global__ void k_stage_merge(GraphDev g, const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                               int64_t n2, const uint32_t *__restrict__ gv, const uint32_t *__restrict__ gstart,
                               const uint32_t *__restrict__ gins, const uint32_t *__restrict__ greloc,
-                              uint32_t *__restrict__ bkeys, GmStatus *st) {
+                              uint32_t *__restrict__ bkeys, uint8_t *__restrict__ ulab, GmStatus *st) {
   if (*(volatile int32_t *)&st->err) return;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -419,8 +432,14 @@ __global__ void k_stage_merge(GraphDev g, const uint64_t *__restrict__ keys, con
         uint32_t d = base + lane;
         if (d < tot) {
           uint32_t i = merge_path(A, na, B, ni, d), j = d - i;
-          if (i < na && (j >= ni || A[i] < B[j])) O[d] = A[i];
-          else { O[d] = B[j]; g.etag[off + d] = vals[start + j]; }
+          if (i < na && (j >= ni || A[i] < B[j])) {
+            O[d] = A[i];
+            if (g.elab) g.elab[off + d] = g.elab[a.x + i];
+          } else {
+            O[d] = B[j];
+            g.etag[off + d] = vals[start + j];
+            if (g.elab) g.elab[off + d] = ulab[vals[start + j] >> 1];
+          }
         }
       }
     } else if (ni) {
@@ -430,17 +449,24 @@ __global__ void k_stage_merge(GraphDev g, const uint64_t *__restrict__ keys, con
         int64_t dd = (int64_t)tot - 1 - base - lane;
         bool act = dd >= 0;
         uint32_t val = 0, tag = 0;
+        uint8_t lab = 0;
         bool fromB = false;
         if (act) {
           uint32_t d = (uint32_t)dd;
           uint32_t i = merge_path(A, na, B, ni, d), j = d - i;
-          if (i < na && (j >= ni || A[i] < B[j])) val = A[i];
-          else { val = B[j]; tag = vals[start + j]; fromB = true; }
+          if (i < na && (j >= ni || A[i] < B[j])) {
+            val = A[i];
+            if (g.elab) lab = g.elab[a.x + i];
+          } else {
+            val = B[j]; tag = vals[start + j]; fromB = true;
+            if (g.elab) lab = ulab[tag >> 1];
+          }
         }
         __syncwarp();
         if (act) {
           O[dd] = val;
           if (fromB) g.etag[off + dd] = tag;
+          if (g.elab) g.elab[off + dd] = lab;
         }
         __syncwarp();
       }
@@ -454,6 +480,7 @@ __global__ void k_stage_merge(GraphDev g, const uint64_t *__restrict__ keys, con
       if (p < tot && (L[p] >> 1) == (k32 >> 1)) {  // always true for a validated batch
         g.col[off + p] = k32 | 1u;
         g.etag[off + p] = vals[j];
+        if (g.elab) ulab[vals[j] >> 1] = g.elab[off + p];  // the deleted edge's label
       }
     }
     __syncwarp();
@@ -478,14 +505,20 @@ __global__ void k_commit(GraphDev g, const uint32_t *__restrict__ gv, const uint
     for (uint32_t base = 0; base < a.y; base += 32) {
       uint32_t i = base + lane;
       uint32_t e = 0;
+      uint8_t lab = 0;
       bool keep = false;
       if (i < a.y) {
         e = L[i];
         keep = !((e & 1u) && (g.etag[a.x + i] & 1u));
+        if (g.elab) lab = g.elab[a.x + i];
       }
       unsigned mask = __ballot_sync(GM_FULL, keep);
       __syncwarp();
-      if (keep) L[out + __popc(mask & ((1u << lane) - 1u))] = e & ~1u;
+      if (keep) {
+        const uint32_t to = out + __popc(mask & ((1u << lane) - 1u));
+        L[to] = e & ~1u;
+        if (g.elab) g.elab[a.x + to] = lab;
+      }
       out += __popc(mask);
       __syncwarp();
     }
@@ -515,20 +548,25 @@ inline int grid_for(int64_t n, int threads) {
 // --------------------------------------------------------------------------
 // host wrappers
 // --------------------------------------------------------------------------
-int gm_load_validate(const int32_t *labels, int32_t n, const int32_t *src, const int32_t *dst, int64_t m,
-                     GmStatus *st, cudaStream_t s) {
-  k_load_validate<<<grid_for(n > m ? n : m, 256), 256, 0, s>>>(labels, n, src, dst, m, st);
+int gm_load_validate(const int32_t *labels, int32_t n, const int32_t *src, const int32_t *dst,
+                     const int32_t *elabels, int64_t m, GmStatus *st, cudaStream_t s) {
+  k_load_validate<<<grid_for(n > m ? n : m, 256), 256, 0, s>>>(labels, n, src, dst, elabels, m, st);
   GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   return GAMMA_OK;
 }
 
-int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m, uint32_t **col_out,
-                  uint32_t **etag_out, uint32_t *pool_cap_out, double pool_factor, uint64_t pool_reserve,
-                  GmStatus *st, GmStatus *h_st, cudaStream_t s) {
+int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, const int32_t *elabels, int64_t m,
+                  uint32_t **col_out, uint32_t **etag_out, uint8_t **elab_out, uint32_t *pool_cap_out,
+                  double pool_factor, uint64_t pool_reserve, GmStatus *st, GmStatus *h_st, cudaStream_t s) {
   const int64_t n2 = 2 * m;
   uint64_t *keys = nullptr, *tk = nullptr;
   uint32_t *flag = nullptr, *pos = nullptr, *deg = nullptr, *rowstart = nullptr, *off = nullptr;
+  uint32_t *vals = nullptr, *tv = nullptr;  // edge labels riding with the keys (labelled graphs)
+  if (elabels) {
+    GM_CUDA(cudaMallocAsync((void **)&vals, sizeof(uint32_t) * (n2 + 1), s));
+    GM_CUDA(cudaMallocAsync((void **)&tv, sizeof(uint32_t) * (n2 + 1), s));
+  }
   GM_CUDA(cudaMallocAsync((void **)&keys, sizeof(uint64_t) * (n2 + 1), s));
   GM_CUDA(cudaMallocAsync((void **)&tk, sizeof(uint64_t) * (n2 + 1), s));
   GM_CUDA(cudaMallocAsync((void **)&flag, sizeof(uint32_t) * (n2 + 1), s));
@@ -538,12 +576,12 @@ int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m,
   GM_CUDA(cudaMallocAsync((void **)&off, sizeof(uint32_t) * (g.n + 1), s));
   GM_CUDA(cudaMemsetAsync(deg, 0, sizeof(uint32_t) * (g.n + 1), s));
   if (m > 0) {
-    k_load_keys<<<grid_for(m, 256), 256, 0, s>>>(src, dst, m, g.label, g.idb, keys);
+    k_load_keys<<<grid_for(m, 256), 256, 0, s>>>(src, dst, elabels, m, g.label, g.idb, keys, vals);
     GM_LAUNCHED();
     GM_CUDA(cudaGetLastError());
-    int rc = gm_radix_sort(keys, nullptr, tk, nullptr, n2, 1, 32 + g.idb, s);
+    int rc = gm_radix_sort(keys, vals, tk, tv, n2, 1, 32 + g.idb, s);
     if (rc) return rc;
-    k_load_uniq<<<grid_for(n2, 256), 256, 0, s>>>(keys, n2, flag, deg);
+    k_load_uniq<<<grid_for(n2, 256), 256, 0, s>>>(keys, vals, n2, flag, deg, st);
     GM_LAUNCHED();
     GM_CUDA(cudaGetLastError());
     rc = gm_scan_excl_u32(flag, pos, n2, s);
@@ -565,10 +603,12 @@ int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m,
   uint64_t cap = (uint64_t)(used * pool_factor) + pool_reserve + 64;
   if (cap >= (1ull << 32) - 64) return GAMMA_ENOMEM;
   uint32_t *col = nullptr, *etag = nullptr;
+  uint8_t *elab = nullptr;
   GM_CUDA(cudaMalloc((void **)&col, sizeof(uint32_t) * (cap + GM_COL_PAD)));  // padded: short lists are read in 16-byte words
   GM_CUDA(cudaMalloc((void **)&etag, sizeof(uint32_t) * cap));
+  if (elabels) GM_CUDA(cudaMalloc((void **)&elab, cap + GM_COL_PAD));
   if (m > 0) {
-    k_load_scatter<<<grid_for(n2, 256), 256, 0, s>>>(keys, n2, flag, pos, rowstart, off, col);
+    k_load_scatter<<<grid_for(n2, 256), 256, 0, s>>>(keys, vals, n2, flag, pos, rowstart, off, col, elab);
     GM_LAUNCHED();
     GM_CUDA(cudaGetLastError());
   }
@@ -579,8 +619,11 @@ int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m,
   GM_CUDA(cudaFreeAsync(deg, s));
   GM_CUDA(cudaFreeAsync(rowstart, s));
   GM_CUDA(cudaFreeAsync(off, s));
+  if (vals) GM_CUDA(cudaFreeAsync(vals, s));
+  if (tv) GM_CUDA(cudaFreeAsync(tv, s));
   *col_out = col;
   *etag_out = etag;
+  *elab_out = elab;
   *pool_cap_out = (uint32_t)cap;
   return GAMMA_OK;
 }
@@ -608,8 +651,8 @@ int gm_hub(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32
   return GAMMA_OK;
 }
 
-int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, int64_t b, const uint32_t *req,
-             StageBufs &sb, GmStatus *st, cudaStream_t s) {
+int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, const int32_t *elab_in, int64_t b,
+             const uint32_t *req, StageBufs &sb, GmStatus *st, cudaStream_t s) {
   const int64_t n2 = 2 * b;
   int rc = GAMMA_OK;
   if (req) {  // chains of updates on one edge across requests (the sort buffers serve as scratch)
@@ -623,7 +666,7 @@ int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *ds
     GM_CUDA(cudaGetLastError());
   }
   k_stage_prep<<<grid_for(b, 256), 256, 0, s>>>(op, src, dst, b, g, sb.cu, sb.cv, sb.cop, sb.keys, sb.vals,
-                                                req ? sb.cinfo : nullptr, st);
+                                                req ? sb.cinfo : nullptr, elab_in, sb.ulab, st);
   GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   rc = gm_radix_sort(sb.keys, sb.vals, sb.tk, sb.tv, n2, 1, 33 + g.idb, s);
@@ -646,7 +689,8 @@ int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *ds
   int64_t mb = (n2 * 32 + 255) / 256;
   if (mb > 16384) mb = 16384;
   if (mb < 1) mb = 1;
-  k_stage_merge<<<(int)mb, 256, 0, s>>>(g, sb.keys, sb.vals, n2, sb.gv, sb.gstart, sb.gins, sb.greloc, sb.bkeys, st);
+  k_stage_merge<<<(int)mb, 256, 0, s>>>(g, sb.keys, sb.vals, n2, sb.gv, sb.gstart, sb.gins, sb.greloc, sb.bkeys,
+                                        sb.ulab, st);
   GM_LAUNCHED();
   GM_CUDA(cudaGetLastError());
   rc = gm_nlf(g, sb.gv, &st->ntouched, (uint32_t)n2, s);

@@ -16,25 +16,30 @@ struct StageBufs {
   // in index order; only its first update (the head) enters the adjacency
   uint32_t *cnext = nullptr;  // [b] next update of the same edge, or ~0
   uint8_t *cinfo = nullptr;   // [b] GM_CHAIN_* bits
+  // edge-labelled graphs: the label of each update's edge (an insertion's
+  // given label; a deletion's label in G, read while staging)
+  uint8_t *ulab = nullptr;    // [b]
   int64_t cap = 0;  // updates
 };
 #define GM_CHAIN_HEAD 1u      // the update is the first of its edge's chain
 #define GM_CHAIN_LONG 2u      // (head) later updates of the same edge follow
 #define GM_CHAIN_PRESENT 4u   // (head) the edge exists once the whole chain is applied
 
-int gm_load_validate(const int32_t *labels, int32_t n, const int32_t *src, const int32_t *dst, int64_t m,
-                     GmStatus *st, cudaStream_t s);
-int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, int64_t m, uint32_t **col_out,
-                  uint32_t **etag_out, uint32_t *pool_cap_out, double pool_factor, uint64_t pool_reserve,
-                  GmStatus *st, GmStatus *h_st, cudaStream_t s);
+// elabels: [m] edge labels in [0, 255] (null: an unlabelled graph)
+int gm_load_validate(const int32_t *labels, int32_t n, const int32_t *src, const int32_t *dst,
+                     const int32_t *elabels, int64_t m, GmStatus *st, cudaStream_t s);
+int gm_load_build(GraphDev g, const int32_t *src, const int32_t *dst, const int32_t *elabels, int64_t m,
+                  uint32_t **col_out, uint32_t **etag_out, uint8_t **elab_out, uint32_t *pool_cap_out,
+                  double pool_factor, uint64_t pool_reserve, GmStatus *st, GmStatus *h_st, cudaStream_t s);
 int gm_nlf(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32_t nverts_max, cudaStream_t s);
 int gm_hub(GraphDev g, const uint32_t *verts, const uint32_t *nverts_dev, uint32_t nverts_max, GmStatus *st,
            cudaStream_t s);
 // req: [b] request of each update when several requests are staged together
 // (null: one request); then updates of different requests may touch the same
 // edge, each request valid on the graph the earlier ones leave
-int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, int64_t b, const uint32_t *req,
-             StageBufs &sb, GmStatus *st, cudaStream_t s);
+// elab_in: [b] insertion labels (edge-labelled graphs; null: all 0)
+int gm_stage(GraphDev g, const int8_t *op, const int32_t *src, const int32_t *dst, const int32_t *elab_in, int64_t b,
+             const uint32_t *req, StageBufs &sb, GmStatus *st, cudaStream_t s);
 int gm_commit(GraphDev g, const StageBufs &sb, int64_t b, bool chains, GmStatus *st, cudaStream_t s);
 // per-query form: the next DFS launch starts at the items the next seed launch appends
 int gm_begin_group(GmStatus *st, cudaStream_t s);
@@ -44,6 +49,7 @@ struct MatchArgs {
   GraphDev g;
   const uint32_t *cu, *cv;     // canonical endpoints per update
   const int8_t *op;
+  const uint8_t *ulab;         // [b] label of each update's edge (edge-labelled graphs), else null
   int64_t b;
   const Plan *plans;
   int nplans;

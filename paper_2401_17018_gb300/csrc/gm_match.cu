@@ -83,18 +83,19 @@ __device__ __forceinline__ uint32_t probe_bytes(uint32_t d) {
 // a hash-indexed list, else {list offset, length | GM_DESC_LIST}.
 #define GM_DESC_LIST 0x80000000u
 __device__ __forceinline__ uint2 edge_desc(const GraphDev &g, uint32_t w) {
-  const uint2 t = __ldg(g.hub_tab + w);
+  const uint2 t = g.elab ? make_uint2(0, 0) : __ldg(g.hub_tab + w);  // hash sets hold keys only, not labels
   if (t.y) return t;
   const uint2 a = __ldg(reinterpret_cast<const uint2 *>(g.adj) + w);
   return make_uint2(a.x, a.y | GM_DESC_LIST);
 }
 
-// is the edge (w, c) visible in the seed's view under the charging rule?
-// x = adjacency key of c (flag bit ignored), D = edge_desc(g, w)
+// is the edge (w, c) visible in the seed's view under the charging rule, and,
+// in an edge-labelled graph, labelled el?  x = adjacency key of c (flag bit
+// ignored), D = edge_desc(g, w)
 template <bool C>
-__device__ __forceinline__ bool edge_ok_d(const GraphDev &g, uint32_t w, uint2 D, uint32_t x, uint32_t sdel,
-                                          uint32_t upd, const uint32_t *req, uint32_t r, const uint32_t *cnext,
-                                          const int8_t *op, ByteCount<C> &bytes) {
+__device__ __forceinline__ bool edge_ok_d(const GraphDev &g, uint32_t w, uint2 D, uint32_t x, uint32_t el,
+                                          uint32_t sdel, uint32_t upd, const uint32_t *req, uint32_t r,
+                                          const uint32_t *cnext, const int8_t *op, ByteCount<C> &bytes) {
   const uint32_t key = x & ~1u;
   uint2 a;
   if (!(D.y & GM_DESC_LIST)) {
@@ -139,6 +140,7 @@ __device__ __forceinline__ bool edge_ok_d(const GraphDev &g, uint32_t w, uint2 D
     }
     bytes += 16u * ((end + 3) / 4) + 8u;
     if (hit < 0) return false;
+    if (g.elab && __ldg(g.elab + a.x + hit) != el) return false;
     if (hy & 1u) return tag_ok(__ldg(g.etag + a.x + hit), sdel, upd, req, r, cnext, op);
     return true;
   }
@@ -148,15 +150,16 @@ __device__ __forceinline__ bool edge_ok_d(const GraphDev &g, uint32_t w, uint2 D
   if (p >= a.y) return false;
   uint32_t y = __ldg(L + p);
   if ((y | 1u) != (key | 1u)) return false;
+  if (g.elab && __ldg(g.elab + a.x + p) != el) return false;
   if (y & 1u) return tag_ok(__ldg(g.etag + a.x + p), sdel, upd, req, r, cnext, op);
   return true;
 }
 
 template <bool C>
-__device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t x, uint32_t sdel,
+__device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t x, uint32_t el, uint32_t sdel,
                                         uint32_t upd, const uint32_t *req, uint32_t r, const uint32_t *cnext,
                                         const int8_t *op, ByteCount<C> &bytes) {
-  return edge_ok_d(g, w, edge_desc(g, w), x, sdel, upd, req, r, cnext, op, bytes);
+  return edge_ok_d(g, w, edge_desc(g, w), x, el, sdel, upd, req, r, cnext, op, bytes);
 }
 
 __device__ __forceinline__ bool nlf_ok(const GraphDev &g, uint32_t v, const Plan &P, int pos) {
@@ -257,6 +260,7 @@ __global__ void k_seed(MatchArgs a) {
         const int pidx = a.pair_plans[pi];
         const Plan &P = a.plans[pidx];
         if (a.use_filter && !(nlf_ok(g, v1, P, 0) && nlf_ok(g, v2, P, 1))) continue;
+        if (g.elab && a.ulab[k] != P.el[1][0]) continue;  // the update's edge label against the query edge's
         if (P.q == 2) {
           if (pass == 0) {
             my_seeds++;
@@ -787,7 +791,7 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
         auto conflict = [&](uint32_t v, uint32_t mv, uint32_t k_lo, uint32_t k_hi) -> uint32_t {
           const uint32_t kj = gm_key(lab, mv, g.idb);
           if (kj < k_lo || kj > k_hi) return 0u;
-          return edge_ok(g, v, kj, sdel, upd, a.req, rq, a.cnext, a.op, lbytes) ? 1u : 0u;
+          return edge_ok(g, v, kj, 0u, sdel, upd, a.req, rq, a.cnext, a.op, lbytes) ? 1u : 0u;  // unlabelled graphs only
         };
         if (lev < 0) {
           if (lane == 0) {
@@ -874,13 +878,15 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       }
       chunks++;
       uint32_t x = ok ? __ldg(g.col + slot2) : 0u;
+      if (ok && g.elab && __ldg(g.elab + slot2) != P.el[c][drv]) ok = false;  // the driver edge's label
       const uint32_t id = (x >> 1) & g.idmask;
       if (ok && (x & 1u)) ok = tag_ok(__ldg(g.etag + slot2), sdel, upd, a.req, rq, a.cnext, a.op);
       uint32_t hp = 0xFFu;  // position whose membership test was looked up at prepare
       if (!stored && lev >= 0 && H->hoist == lev) {
         const uint4 h = HO[e];
         hp = h.w;
-        if (ok && hp != 0xFFu) ok = edge_ok_d(g, h.x, make_uint2(h.y, h.z), x, sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
+        if (ok && hp != 0xFFu)
+          ok = edge_ok_d(g, h.x, make_uint2(h.y, h.z), x, P.el[c][hp], sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
       }
       const uint16_t chk_edge = P.bwd[c] & (uint16_t)~(1u << drv) & (uint16_t)~(hp < 16u ? (1u << hp) : 0u);
       const bool shared = !stored && lev >= 0 && ((H->coll >> lev) & 1u);
@@ -897,13 +903,14 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
           const int pos = l2 + 2;
           const uint32_t vv = V[l2 * T + ee];
           if ((chk_neq >> pos) & 1) ok = (vv != id);
-          if (ok && ((chk_edge >> pos) & 1)) ok = edge_ok(g, vv, x, sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
+          if (ok && ((chk_edge >> pos) & 1))
+            ok = edge_ok(g, vv, x, P.el[c][pos], sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
           ee = PAR[l2 * T + ee];
         }
         if (ok && ((chk_neq >> 1) & 1)) ok = (m1 != id);
-        if (ok && ((chk_edge >> 1) & 1)) ok = edge_ok(g, m1, x, sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
+        if (ok && ((chk_edge >> 1) & 1)) ok = edge_ok(g, m1, x, P.el[c][1], sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
         if (ok && (chk_neq & 1)) ok = (m0 != id);
-        if (ok && (chk_edge & 1)) ok = edge_ok(g, m0, x, sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
+        if (ok && (chk_edge & 1)) ok = edge_ok(g, m0, x, P.el[c][0], sdel, upd, a.req, rq, a.cnext, a.op, lbytes);
       }
       if (ok && stored && a.use_filter) ok = nlf_ok(g, id, P, c);
       if (gidx < total) lbytes += ((x & 1u) ? 8u : 4u) + (ok ? 8u : 0u);

@@ -79,6 +79,9 @@ _SIGS = {
     "gamma_create": (ctypes.c_int, [ctypes.POINTER(gamma_options), ctypes.POINTER(ctypes.c_void_p)]),
     "gamma_destroy": (None, [_P]),
     "gamma_load_graph": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P]),
+    "gamma_load_graph_el": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P]),
+    "gamma_register_query_el": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P, _P, _P]),
+    "gamma_apply_batch_el": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P, ctypes.c_int32, _P, _P, _P, _P]),
     "gamma_register_query": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "gamma_apply_batch": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int32, _P, _P, _P,
@@ -179,33 +182,65 @@ def gamma_destroy(ctx: int) -> None:
     load_library().gamma_destroy(ctx)
 
 
-def gamma_load_graph(ctx: int, n: int, labels, src, dst) -> None:
+def gamma_load_graph(ctx: int, n: int, labels, src, dst, elabels=None) -> None:
+    """elabels (one per edge): an edge-labelled graph (gamma_load_graph_el)."""
     labels, src, dst = _as(labels, np.int32), _as(src, np.int32), _as(dst, np.int32)
-    _check(ctx, load_library().gamma_load_graph(ctx, int(n), _ptr(labels), int(src.shape[0]), _ptr(src), _ptr(dst)))
+    if elabels is None:
+        _check(ctx, load_library().gamma_load_graph(ctx, int(n), _ptr(labels), int(src.shape[0]), _ptr(src),
+                                                    _ptr(dst)))
+    else:
+        el = _as(elabels, np.int32)
+        _check(ctx, load_library().gamma_load_graph_el(ctx, int(n), _ptr(labels), int(src.shape[0]), _ptr(src),
+                                                       _ptr(dst), _ptr(el)))
 
 
-def gamma_register_query(ctx: int, labels, src, dst) -> int:
+def gamma_register_query(ctx: int, labels, src, dst, elabels=None) -> int:
+    """elabels (one per query edge): edge labels (gamma_register_query_el)."""
     labels, src, dst = _as(labels, np.int32), _as(src, np.int32), _as(dst, np.int32)
     qid = ctypes.c_int32(-1)
-    _check(ctx, load_library().gamma_register_query(ctx, int(labels.shape[0]), _ptr(labels), int(src.shape[0]),
-                                                    _ptr(src), _ptr(dst), ctypes.byref(qid)))
+    if elabels is None:
+        _check(ctx, load_library().gamma_register_query(ctx, int(labels.shape[0]), _ptr(labels), int(src.shape[0]),
+                                                        _ptr(src), _ptr(dst), ctypes.byref(qid)))
+    else:
+        el = np.ascontiguousarray(elabels, dtype=np.int32)
+        _check(ctx, load_library().gamma_register_query_el(ctx, int(labels.shape[0]), _ptr(labels),
+                                                           int(src.shape[0]), _ptr(src), _ptr(dst), _ptr(el),
+                                                           ctypes.byref(qid)))
     return qid.value
 
 
-def gamma_apply_batch(ctx: int, op, src, dst, qids: Sequence[int], matches: Optional[gamma_matches] = None
-                      ) -> Tuple[np.ndarray, np.ndarray, int]:
+def gamma_apply_batch(ctx: int, op, src, dst, qids: Sequence[int], matches: Optional[gamma_matches] = None,
+                      elab=None) -> Tuple[np.ndarray, np.ndarray, int]:
     """Returns (pos counts, neg counts, rc); rc is GAMMA_OK or GAMMA_EOVERFLOW
-    (other codes raise)."""
+    (other codes raise).  elab: insertion labels (gamma_apply_batch_el)."""
     op, src, dst = _as(op, np.int8), _as(src, np.int32), _as(dst, np.int32)
     q = np.ascontiguousarray(qids, dtype=np.int32)
     pos = np.zeros(max(q.size, 1), np.uint64)
     neg = np.zeros(max(q.size, 1), np.uint64)
-    rc = load_library().gamma_apply_batch(ctx, int(op.shape[0]), _ptr(op), _ptr(src), _ptr(dst), int(q.size),
-                                          _ptr(q), _ptr(pos), _ptr(neg),
-                                          ctypes.byref(matches) if matches is not None else None)
+    mref = ctypes.byref(matches) if matches is not None else None
+    if elab is None:
+        rc = load_library().gamma_apply_batch(ctx, int(op.shape[0]), _ptr(op), _ptr(src), _ptr(dst), int(q.size),
+                                              _ptr(q), _ptr(pos), _ptr(neg), mref)
+    else:
+        el = _as(elab, np.int32)
+        rc = load_library().gamma_apply_batch_el(ctx, int(op.shape[0]), _ptr(op), _ptr(src), _ptr(dst), _ptr(el),
+                                                 int(q.size), _ptr(q), _ptr(pos), _ptr(neg), mref)
     if rc not in (GAMMA_OK, GAMMA_EOVERFLOW):
         _check(ctx, rc)
     return pos[:q.size], neg[:q.size], rc
+
+
+def gamma_load_graph_el(ctx: int, n: int, labels, src, dst, elabels) -> None:
+    gamma_load_graph(ctx, n, labels, src, dst, elabels)
+
+
+def gamma_register_query_el(ctx: int, labels, src, dst, elabels) -> int:
+    return gamma_register_query(ctx, labels, src, dst, elabels)
+
+
+def gamma_apply_batch_el(ctx: int, op, src, dst, elab, qids: Sequence[int],
+                         matches: Optional[gamma_matches] = None) -> Tuple[np.ndarray, np.ndarray, int]:
+    return gamma_apply_batch(ctx, op, src, dst, qids, matches, elab)
 
 
 def gamma_apply_batches(ctx: int, req_off, op, src, dst, qids: Sequence[int]) -> Tuple[np.ndarray, np.ndarray]:
@@ -366,17 +401,17 @@ class Context:
             setattr(self._opts, "cuda_stream" if k == "stream" else k, v)
         gamma_set_options(self.h, self._opts)
 
-    def load_graph(self, n, labels, src, dst):
-        gamma_load_graph(self.h, n, labels, src, dst)
+    def load_graph(self, n, labels, src, dst, elabels=None):
+        gamma_load_graph(self.h, n, labels, src, dst, elabels)
         self.qsizes = {}
 
-    def register_query(self, labels, src, dst) -> int:
-        qid = gamma_register_query(self.h, labels, src, dst)
+    def register_query(self, labels, src, dst, elabels=None) -> int:
+        qid = gamma_register_query(self.h, labels, src, dst, elabels)
         self.qsizes[qid] = int(len(labels))
         return qid
 
     def apply_batch(self, op, src, dst, qids: Sequence[int], row_capacity: Optional[int] = None,
-                    rows=None):
+                    rows=None, elab=None):
         """Apply a batch. With row_capacity (host rows) or rows (a preallocated
         int32 buffer, host or device, shape [capacity, stride]) the match rows
         are returned too: (pos, neg, rows_written, required)."""
@@ -391,7 +426,7 @@ class Context:
                 buf = rows
                 stride = int(buf.shape[1])
             m = gamma_matches(_ptr(buf), int(buf.shape[0]) if row_capacity is None else int(row_capacity), stride, 0, 0)
-        pos, neg, rc = gamma_apply_batch(self.h, op, src, dst, qids, m)
+        pos, neg, rc = gamma_apply_batch(self.h, op, src, dst, qids, m, elab)
         if m is None:
             return pos, neg
         return pos, neg, buf[:m.written], m.required

@@ -7,8 +7,9 @@ check set is built as the query was selected (``make_queries.py``): every
 down the updates whose endpoint labels match one of the query's edges by
 decreasing product of endpoint degrees in the graph that batch meets, the
 first ``heavy`` the oracle finishes within ``heavy_budget`` candidate tests
-each).  Pairs the oracle cannot finish within their budget are passed over
-and listed in the output; every pair of the check set is exact.  One worker
+each; the walk stops after ``MAX_PASSED`` candidates were passed over).
+Pairs the oracle cannot finish within their budget are passed over and
+listed in the output; every pair of the check set is exact.  One worker
 process per query, batch by batch.  Nothing here touches the CUDA path.
 
 Batches: large -- the five consecutive batches of 800,000 insertions and
@@ -39,6 +40,9 @@ from oracle import oracle as O  # noqa: E402
 from paper_2401_17018_gb300 import inputs as I  # noqa: E402
 
 SERVED_REQUESTS = 4
+# heavy candidates over budget passed over per (query, batch) before the walk
+# stops (the check set then holds fewer heavy updates)
+MAX_PASSED = 24
 
 _S = None
 
@@ -59,7 +63,8 @@ def file_digest(path):
 
 def _job(j):
     sess, queries, table, prod, sample, spec = _S
-    got, heavy, passed, _ = MQ.check_pairs(sess, queries[j], table, prod, sample, spec, strict_sample=False)
+    got, heavy, passed, _ = MQ.check_pairs(sess, queries[j], table, prod, sample, spec, strict_sample=False,
+                                           max_passed=MAX_PASSED)
     return j, got, heavy, passed
 
 
@@ -82,8 +87,9 @@ def main():
            "rule": "per batch and query: every %d-th update (within %d candidate tests each) and the %d heaviest "
                    "verifiable updates (going down the updates whose endpoint labels match one of the query's edges "
                    "by decreasing endpoint-degree product in the graph the batch meets, the first %d the oracle "
-                   "finishes within %d candidate tests each); pairs over budget are passed over and listed" % (
-                       spec["stride"], spec["sample_budget"], spec["heavy"], spec["heavy"], spec["heavy_budget"]),
+                   "finishes within %d candidate tests each, stopping after %d passed over); pairs over budget are "
+                   "passed over and listed" % (spec["stride"], spec["sample_budget"], spec["heavy"], spec["heavy"],
+                                               spec["heavy_budget"], MAX_PASSED),
            "batches": []}
     src, dst = w.graph.src, w.graph.dst
     t0 = time.time()

@@ -112,12 +112,14 @@ def heavy_candidates(q, table, prod):
     return sorted(cand, key=lambda k: (-prod[k], k))
 
 
-def check_pairs(sess, Q, table, prod, sample, spec, strict_sample):
+def check_pairs(sess, Q, table, prod, sample, spec, strict_sample, max_passed=None):
     """Evaluate Q's check set on one batch, one pair at a time: the sampled
     updates within the sample budget, then the heaviest verifiable updates.
     Returns (counts by update, heavy updates, passed-over updates, reason):
     reason is None when the set is complete; with strict_sample a sampled
-    update over budget is a reason (selection), else it is passed over."""
+    update over budget is a reason (selection), else it is passed over.
+    max_passed: stop looking for heavy updates after that many were passed
+    over (the set then holds fewer)."""
     got, passed = {}, []
     for u in sample.tolist():
         c = int(sess.eval([Q], eval_idx=[u], update_budget=spec["sample_budget"])[0, 0])
@@ -134,6 +136,8 @@ def check_pairs(sess, Q, table, prod, sample, spec, strict_sample):
         if u in got:
             heavy.append(u)
             continue
+        if max_passed is not None and len(passed) >= max_passed:
+            break
         c = int(sess.eval([Q], eval_idx=[u], update_budget=spec["heavy_budget"])[0, 0])
         if c == int(O.NOT_COMPUTED):
             passed.append(u)

@@ -78,6 +78,9 @@ def test_null_handles_are_rejected_without_a_gpu():
         "gamma_register_query": (None, 2, None, 1, None, None, ctypes.byref(i32)),
         "gamma_apply_batch": (None, 0, None, None, None, 0, None, None, None, None),
         "gamma_apply_batches": (None, 1, None, None, None, None, 0, None, None, None),
+        "gamma_load_graph_el": (None, 1, None, 0, None, None, None),
+        "gamma_register_query_el": (None, 2, None, 1, None, None, None, ctypes.byref(i32)),
+        "gamma_apply_batch_el": (None, 0, None, None, None, None, 0, None, None, None, None),
         "gamma_fetch_matches": (None, None),
         "gamma_commit": (None,),
         "gamma_update_counts": (None, 0, None),
