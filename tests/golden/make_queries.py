@@ -18,7 +18,8 @@ only when every pair of its check set can be verified by the CPU oracle:
   over and counted; only the first ``TOP_PER_PAIR`` per label pair are
   tried);
 * the oracle must finish each sampled pair within ``sample_budget``
-  candidate tests, find ``heavy`` verifiable heavy updates, and the check
+  candidate tests, find ``heavy`` verifiable heavy updates (with
+  ``max_passed``: before passing over more than that many), and the check
   set must hold at least one incremental match.
 
 Rejections are counted per class and reason in the output.  Nothing here
@@ -52,7 +53,7 @@ SPECS = {
     # updates verifiable by the oracle.)
     "large": {"workload": "large", "plan": [("sparse", 6)] * 4 + [("dense", 6)] * 4,
               "stride": 20_000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
-              "max_attempts": 4000},
+              "max_passed": 8, "max_attempts": 4000},
     # 20 six-vertex queries, 10 sparse and 10 dense, on the scale-20 graph
     "mid": {"workload": "mid", "plan": [("sparse", 6)] * 10 + [("dense", 6)] * 10,
             "stride": 1000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
@@ -61,7 +62,7 @@ SPECS = {
     # (dense in the paper's sense, average degree >= 3), on the mid graph
     "batched": {"workload": "mid", "plan": [("sparse" if i % 2 == 0 else "dense_ge3", 4 + (i * 7) % 9)
                                             for i in range(64)],
-                "stride": 1000, "sample_budget": 2_000_000, "heavy": 8, "heavy_budget": 20_000_000,
+                "stride": 1000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
                 "max_attempts": 6000},
     # 16 dense queries of 6..8 vertices on the scale-22 served graph; the
     # selection batch has the served stream's 1:1 mix of insertions and
@@ -170,7 +171,8 @@ def _try(args):
     if Q is None:
         return attempt, None, "class test failed"
     t = time.time()
-    got, heavy, passed, why = check_pairs(sess, Q, table, prod, sample, spec, strict_sample=True)
+    got, heavy, passed, why = check_pairs(sess, Q, table, prod, sample, spec, strict_sample=True,
+                                          max_passed=spec.get("max_passed"))
     if why is not None:
         return attempt, None, why
     if sum(got.values()) == 0:
@@ -200,9 +202,10 @@ def main():
     rule = ("keep a candidate when the CPU oracle verifies its check set on the selection batch: every %d-th "
             "update within %d candidate tests each, and the %d heaviest verifiable updates (going down the updates "
             "whose endpoint labels match one of the query's edges by decreasing endpoint-degree product, the first "
-            "%d finished within %d candidate tests each; heavier ones are passed over and counted); the check set "
-            "must hold an incremental match; at most %d attempts per (class, size), no fall to smaller sizes" % (
+            "%d finished within %d candidate tests each; heavier ones are passed over and counted%s); the check "
+            "set must hold an incremental match; at most %d attempts per (class, size), no fall to smaller sizes" % (
                 spec["stride"], spec["sample_budget"], spec["heavy"], spec["heavy"], spec["heavy_budget"],
+                ", at most %d of them" % spec["max_passed"] if spec.get("max_passed") else "",
                 spec["max_attempts"]))
     out = {"workload": spec["workload"], "graph_digest": w.graph.digest(), "selection_batch_updates": len(b),
            "rule": rule, "queries": [], "rejected": {}}
