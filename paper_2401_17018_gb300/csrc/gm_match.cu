@@ -162,6 +162,18 @@ __device__ __forceinline__ bool edge_ok(const GraphDev &g, uint32_t w, uint32_t 
   return edge_ok_d(g, w, edge_desc(g, w), x, el, sdel, upd, req, r, cnext, op, bytes);
 }
 
+// size of N^lab(v) for choosing a driver: the per-label count, exact below
+// 255; a saturated count is made exact from the hash index's label-segment
+// starts, or, for a vertex without one, ranked after every exact size
+__device__ __forceinline__ uint32_t seg_size(const GraphDev &g, uint32_t v, int lab) {
+  const uint32_t c = __ldg(g.nlf + (size_t)v * g.nlfw + lab);
+  if (c < 255u) return c;
+  const int32_t h = __ldg(g.hub_id + v);
+  if (h < 0) return 1u << 30;
+  const uint32_t *o = g.hub_lofs + (size_t)h * (g.nlab + 1) + lab;
+  return __ldg(o + 1) - __ldg(o);
+}
+
 __device__ __forceinline__ bool nlf_ok(const GraphDev &g, uint32_t v, const Plan &P, int pos) {
   const uint8_t *row = g.nlf + (size_t)v * g.nlfw;
   int nr = P.nreq[pos];
@@ -616,17 +628,17 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
             int pos = l2 + 2;
             uint32_t vv = V[l2 * T + e];
             if ((bw >> pos) & 1) {
-              uint32_t c = __ldg(g.nlf + (size_t)vv * g.nlfw + lab);
+              uint32_t c = seg_size(g, vv, lab);
               if (c < best) { best = c; bestv = vv; drv = pos; }
             }
             e = PAR[l2 * T + e];
           }
           if ((bw >> 1) & 1) {
-            uint32_t c = __ldg(g.nlf + (size_t)m1 * g.nlfw + lab);
+            uint32_t c = seg_size(g, m1, lab);
             if (c < best) { best = c; bestv = m1; drv = 1; }
           }
           if (bw & 1) {
-            uint32_t c = __ldg(g.nlf + (size_t)m0 * g.nlfw + lab);
+            uint32_t c = seg_size(g, m0, lab);
             if (c < best) { best = c; bestv = m0; drv = 0; }
           }
           lbytes += 4u * __popc(bw);
