@@ -98,7 +98,7 @@ def _run_batches(G, name, flags=0):
 
 def test_large_workload_five_batches(G):
     """The headline workload: the scale-23 graph (60.4M edges, 16 labels) and
-    its eight 8-vertex queries, five consecutive batches of 800,000
+    its eight 6-vertex queries (4 sparse, 4 dense), five consecutive batches of 800,000
     insertions and 200,000 deletions, each committed before the next."""
     batches, totals, st, pairs, heavy = _run_batches(G, "large")
     assert heavy > 0 and sum(int(p.sum() + n.sum()) for p, n in totals) > 0
