@@ -610,8 +610,8 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
       uint32_t carry = 0;
       for (uint32_t base = 0; base < n; base += 32) {
         uint32_t i = base + lane;
-        uint32_t len = 0, lo = 0;
-        int drv = 0;
+        uint32_t len = 0, lo = 0, v2 = 0;
+        int drv = 0, drv2 = -1;
         bool first = true;
         if (coll && i < n) {
           first = i == 0 || par[i] != par[i - 1];
@@ -621,26 +621,26 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
           MUL[L * T + i] = (uint16_t)(j - i);
         }
         if (i < n && first) {
-          // the backward neighbour with the fewest label-lab neighbours drives
-          uint32_t best = 0xffffffffu, bestv = 0;
+          // the backward neighbour with the fewest label-lab neighbours
+          // drives; the one with the next fewest is tested first
+          uint32_t best = 0xffffffffu, bestv = 0, best2 = 0xffffffffu;
           uint32_t e = i;
+          auto consider = [&](uint32_t vv, int pos) {
+            const uint32_t c = seg_size(g, vv, lab);
+            if (c < best) {
+              if (best != 0xffffffffu) { best2 = best; v2 = bestv; drv2 = drv; }  // the old driver is now second
+              best = c; bestv = vv; drv = pos;
+            } else if (c < best2) {
+              best2 = c; v2 = vv; drv2 = pos;
+            }
+          };
           for (int l2 = L; l2 >= 0; l2--) {
             int pos = l2 + 2;
-            uint32_t vv = V[l2 * T + e];
-            if ((bw >> pos) & 1) {
-              uint32_t c = seg_size(g, vv, lab);
-              if (c < best) { best = c; bestv = vv; drv = pos; }
-            }
+            if ((bw >> pos) & 1) consider(V[l2 * T + e], pos);
             e = PAR[l2 * T + e];
           }
-          if ((bw >> 1) & 1) {
-            uint32_t c = seg_size(g, m1, lab);
-            if (c < best) { best = c; bestv = m1; drv = 1; }
-          }
-          if (bw & 1) {
-            uint32_t c = seg_size(g, m0, lab);
-            if (c < best) { best = c; bestv = m0; drv = 0; }
-          }
+          if ((bw >> 1) & 1) consider(m1, 1);
+          if (bw & 1) consider(m0, 0);
           lbytes += 4u * __popc(bw);
           if (best > 0) label_segment(g, bestv, lab, lo, len, lbytes);
         }
@@ -649,23 +649,16 @@ __global__ void __maxnreg__(64) k_dfs(MatchArgs a) {
           DRV[L * T + i] = (uint8_t)drv;
         }
         if (np == last && i < n && first) {
-          // the first membership test of the last position (its highest
-          // backward neighbour other than the driver), looked up once here
-          const uint32_t chk = (uint32_t)bw & ~(1u << drv);
-          uint32_t w = 0, hp = 0xFFu;
+          // the first membership test of the last position (the backward
+          // neighbour other than the driver with the fewest label-lab
+          // neighbours, the likeliest to reject), looked up once here
+          uint32_t hp = 0xFFu;
           uint2 D = make_uint2(0, 0);
-          if (chk && len) {
-            hp = 31u - __clz(chk);
-            if (hp >= 2) {
-              uint32_t ee = i;
-              for (int l2 = L; l2 > (int)hp - 2; l2--) ee = PAR[l2 * T + ee];
-              w = V[(hp - 2) * T + ee];
-            } else {
-              w = hp ? m1 : m0;
-            }
-            D = edge_desc(g, w);
+          if (drv2 >= 0 && len) {
+            hp = (uint32_t)drv2;
+            D = edge_desc(g, v2);
           }
-          HO[i] = make_uint4(w, D.x, D.y, hp);
+          HO[i] = make_uint4(hp == 0xFFu ? 0u : v2, D.x, D.y, hp);
         }
         uint32_t inc = len;
         for (int d = 1; d < 32; d <<= 1) {

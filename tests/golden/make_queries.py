@@ -62,7 +62,7 @@ SPECS = {
     # (dense in the paper's sense, average degree >= 3), on the mid graph
     "batched": {"workload": "mid", "plan": [("sparse" if i % 2 == 0 else "dense_ge3", 4 + (i * 7) % 9)
                                             for i in range(64)],
-                "stride": 1000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
+                "stride": 10_000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
                 "max_passed": 8, "max_attempts": 6000},
     # 16 sparse queries of 6..8 vertices on the scale-22 served graph; the
     # selection batch has the served stream's 1:1 mix of insertions and
@@ -70,7 +70,7 @@ SPECS = {
     # none of 432 six-vertex candidates had its sampled updates within the
     # sample budget and eight heavy updates verifiable.)
     "served": {"workload": "served", "plan": [("sparse", 6 + i % 3) for i in range(16)],
-               "stride": 1000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
+               "stride": 10_000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
                "max_passed": 8, "max_attempts": 6000},
 }
 TOP_PER_PAIR = 64  # heavy candidates kept per endpoint-label pair
@@ -194,6 +194,7 @@ def main():
     ap.add_argument("name", choices=sorted(SPECS))
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--kind", default=None, help="select only this class (the partial results are merged by --merge)")
+    ap.add_argument("--sizes", default=None, help="select only these sizes, e.g. 7,8 (with --kind)")
     ap.add_argument("--merge", action="store_true", help="merge the per-class partial files into the output")
     args = ap.parse_args()
     spec = SPECS[args.name]
@@ -212,8 +213,9 @@ def main():
     out = {"workload": spec["workload"], "graph_digest": w.graph.digest(), "selection_batch_updates": len(b),
            "rule": rule, "queries": [], "rejected": {}}
     want = {}
+    sizes = {int(x) for x in args.sizes.split(",")} if args.sizes else None
     for kind, q in spec["plan"]:
-        if args.kind is None or kind == args.kind:
+        if (args.kind is None or kind == args.kind) and (args.sizes is None or q in sizes):
             want[(kind, q)] = want.get((kind, q), 0) + 1
     chosen = {c: [] for c in want}
     seen = set()
@@ -247,7 +249,8 @@ def main():
                     len(got), need, kind, q, attempt))
     if args.kind is not None:  # one class: a partial file, merged later
         out["chosen"] = {"%s:%d" % k: v for k, v in chosen.items()}
-        path = os.path.join(HERE, "queries_%s.%s.partial" % (args.name, args.kind))
+        path = os.path.join(HERE, "queries_%s.%s%s.partial" % (
+            args.name, args.kind, ".q" + "-".join(str(q) for q in sorted(sizes)) if sizes else ""))
         with open(path, "w") as f:
             json.dump(out, f, indent=1)
         print("wrote", path, "in %.0f s" % (time.time() - t0))
@@ -264,17 +267,22 @@ def main():
 
 
 def merge(name):
-    """Assemble queries_NAME.json from the per-class partial files."""
+    """Assemble queries_NAME.json from the partial files (one per class, or
+    per class and sizes)."""
     spec = SPECS[name]
     chosen, rejected, head = {}, {}, None
-    for kind in sorted({k for k, _ in spec["plan"]}):
-        with open(os.path.join(HERE, "queries_%s.%s.partial" % (name, kind))) as f:
+    parts = sorted(f for f in os.listdir(HERE) if f.startswith("queries_%s." % name) and f.endswith(".partial"))
+    for fn in parts:
+        with open(os.path.join(HERE, fn)) as f:
             d = json.load(f)
         head = head or d
         rejected.update(d["rejected"])
         for key, v in d["chosen"].items():
             k, q = key.split(":")
             chosen[(k, int(q))] = v
+    keys = [json.dumps([d["labels"], d["edges"]]) for v in chosen.values() for d in v]
+    if len(set(keys)) != len(keys):
+        raise SystemExit("the partial files hold the same query twice")
     out = {k: head[k] for k in ("workload", "graph_digest", "selection_batch_updates", "rule")}
     out["queries"], out["rejected"] = [], rejected
     used = {}
