@@ -63,6 +63,9 @@ extern "C" {
 #define GAMMA_F_NO_SHARE 0x40u  /* expand every partial match at the last query vertex (default: when that
                                    vertex is not adjacent to the one before it and no rows are requested,
                                    the children of one partial match share their candidates) */
+#define GAMMA_F_SEED_IN_ORDER 0x80u /* create DFS work in update order (default with one staged request:
+                                   grouped by each update's higher-degree endpoint, so that warps running
+                                   together search around the same vertex); results are the same */
 
 typedef struct gamma_ctx gamma_ctx;
 

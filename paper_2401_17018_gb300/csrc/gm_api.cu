@@ -495,6 +495,9 @@ int enqueue_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_s
   a.gstart = ctx->sb.gstart;
   a.gins = ctx->sb.gins;
   a.n2 = (uint32_t)(2 * b);
+  // the sorted batch holds both entries of every update only when one request is staged
+  // (a later update of an edge shared by several requests has none)
+  a.seed_sorted = (ctx->nreq <= 1 && !(ctx->flags & GAMMA_F_SEED_IN_ORDER)) ? 1 : 0;
   a.tasks = ctx->d_tasks;
   a.sched = ctx->d_sched;
   a.task_seq = ctx->d_task_seq;
@@ -842,6 +845,7 @@ int gm_recount_prepare(gamma_ctx *ctx, MatchArgs *a, int *nslots, int *num_sms, 
   m.g = ctx->gd();
   m.cu = ctx->sb.cu; m.cv = ctx->sb.cv; m.op = ctx->sb.cop; m.b = ctx->b;
   m.ulab = ctx->d_elab ? ctx->sb.ulab : nullptr;
+  m.seed_sorted = 0;  // the recount reuses the staged batch's work items; it seeds nothing
   m.plans = ctx->d_plans; m.nplans = ctx->nplans;
   m.pair_off = ctx->d_pair_off; m.pair_plans = ctx->d_pair_plans;
   m.grain = ctx->grain;

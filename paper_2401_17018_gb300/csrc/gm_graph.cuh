@@ -74,6 +74,8 @@ struct MatchArgs {
   int count_bytes;             // accumulate algorithmic bytes into st->alg_bytes
   int leaf;                    // count a last position with one backward neighbour in closed form
   int share;                   // siblings share last-position candidates (counts only)
+  int seed_sorted;             // seed in the order of the sorted batch, each update at its
+                               // higher-degree endpoint (needs both entries of every update)
   const uint64_t *bkeys;       // the staged batch, sorted: (vertex << 33 | deletion << 32 | key)
   const uint32_t *bvals;       // its tags
   const uint32_t *gstart;      // [groups] first sorted entry of each touched vertex

@@ -236,10 +236,30 @@ __global__ void k_seed(MatchArgs a) {
   if (*(volatile int32_t *)&st->err) return;
   const int lane = threadIdx.x & 31;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // Work items come out in seeding order, and the DFS warps take them in
+  // that order.  With seed_sorted, thread t takes entry t of the batch sorted
+  // by vertex and seeds the update there only if that vertex is the
+  // update's endpoint of higher degree (ties: smaller id): the updates at one
+  // hub then sit together, so warps that run at the same time search around
+  // the same hub and share its lists and hash set in L2.
+  const int64_t nit = a.seed_sorted ? (int64_t)a.n2 : a.b;
   // grid-stride loop with a warp-uniform trip count for the warp-aggregated atomics
-  int64_t b_round = ((a.b + 31) / 32) * 32;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b_round; k += stride) {
-    const bool act = k < a.b;
+  int64_t b_round = ((nit + 31) / 32) * 32;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < b_round; t += stride) {
+    bool act = t < nit;
+    int64_t k = t;
+    if (act && a.seed_sorted) {
+      const uint64_t key = a.bkeys[t];
+      if (key == ~0ull) {
+        act = false;
+      } else {
+        k = (int64_t)(a.bvals[t] >> 1);
+        const uint32_t x = (uint32_t)(key >> 33);
+        const uint32_t y = (a.cu[k] == x) ? a.cv[k] : a.cu[k];
+        const uint32_t dx = a.g.adj[x].y, dy = a.g.adj[y].y;
+        act = dx > dy || (dx == dy && x < y);
+      }
+    }
     uint32_t v1 = 0, v2 = 0, sdel = 0;
     uint32_t p0 = 0, p1 = 0;
     if (act) {
@@ -1026,7 +1046,8 @@ size_t gm_dfs_smem_per_warp(int tile, int nlev) { return smem_per_warp(tile, nle
 int gm_seed(const MatchArgs &a, cudaStream_t s) {
   if (a.b <= 0 || a.nplans <= 0) return GAMMA_OK;
   int threads = 256;
-  int64_t blocks = (a.b + threads - 1) / threads;
+  const int64_t nit = a.seed_sorted ? (int64_t)a.n2 : a.b;
+  int64_t blocks = (nit + threads - 1) / threads;
   if (blocks > 65536) blocks = 65536;
   k_seed<<<(int)blocks, threads, 0, s>>>(a);
   GM_LAUNCHED();
