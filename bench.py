@@ -484,7 +484,7 @@ def run_served(args):
         runs["%.2f" % load] = dict(per_form, identical_counts=same)
     line = {"metric": "served form: p50/p99 batch latency from arrival and sustained updates/s (1 GB300)",
             "mode": "served",
-            "config": {"workload": "served: R-MAT scale 22, 8 uniform labels, %d %s queries of %d..%d "
+            "config": {"workload": "served: R-MAT scale 22, 8 labels Zipf(1.2), %d %s queries of %d..%d "
                                    "vertices, %d batches of floor(10^U(%g,%g)) updates (ins:del 1:1), Poisson "
                                    "arrivals" % (len(queries), "/".join(sorted({q.kind for q in queries})),
                                                  min(q.labels.size for q in queries),

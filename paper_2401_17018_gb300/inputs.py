@@ -336,6 +336,8 @@ def random_walk_query(off: np.ndarray, nbr: np.ndarray, labels: np.ndarray, q: i
     further induced edges up to |E| = min(#induced, q + r) with r in
     [0, q/2] drawn per attempt, so the average degree is <= 3 and the query
     has at least one cycle; it is None when the induced subgraph is a tree.
+    "sparse_lt3": the same with average degree < 3, the complement of
+    "dense_ge3" (a query of exactly 3 belongs to dense_ge3 only).
     Labels are inherited. Returns None when the class test fails.
     """
     n = off.size - 1
@@ -423,6 +425,8 @@ def random_walk_query(off: np.ndarray, nbr: np.ndarray, labels: np.ndarray, q: i
             edges = sorted(tree + rest[:extra])
             if not (len(edges) >= q and 2.0 * len(edges) / q <= 3.0):
                 return None
+            if kind == "sparse_lt3" and 2.0 * len(edges) / q >= 3.0:
+                return None
     e = np.array(edges, dtype=np.int32).reshape(-1, 2)
     return Query(labels[np.array(order)].astype(np.int32), e[:, 0].copy(), e[:, 1].copy(), kind)
 
@@ -460,7 +464,7 @@ WORKLOADS = {
     "tiny": (11, 10_000, 4, None, 1),
     "mid": (20, 8_388_608, 8, 1.2, 1),
     "large": (23, 67_108_864, 16, 1.0, 1),
-    "served": (22, 33_554_432, 8, None, 1),
+    "served": (22, 33_554_432, 8, 1.2, 1),
 }
 
 

@@ -58,18 +58,20 @@ SPECS = {
     "mid": {"workload": "mid", "plan": [("sparse", 6)] * 10 + [("dense", 6)] * 10,
             "stride": 1000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
             "max_attempts": 4000},
-    # 64 queries of 4..12 vertices (uneven sizes), sparse and dense alternating
-    # (dense in the paper's sense, average degree >= 3), on the mid graph
-    "batched": {"workload": "mid", "plan": [("sparse" if i % 2 == 0 else "dense_ge3", 4 + (i * 7) % 9)
-                                            for i in range(64)],
+    # 64 queries, sparse (average degree < 3) of 4..6 vertices and dense
+    # (average degree >= 3, the paper's Dense class) of 4..8 vertices
+    # alternating, on the mid graph.  Larger ones were not verifiable: of 20
+    # dense 9-vertex and 264 sparse 9-vertex candidates and 72 sparse
+    # 7-vertex ones, none had its sampled and eight heavy updates within the
+    # budgets.
+    "batched": {"workload": "mid", "plan": [("sparse_lt3", 4 + (i // 2) % 3) if i % 2 == 0
+                                            else ("dense_ge3", 4 + (i // 2) % 5) for i in range(64)],
                 "stride": 10_000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
                 "max_passed": 8, "max_attempts": 6000},
-    # 16 sparse queries of 6..8 vertices on the scale-22 served graph; the
+    # 16 dense queries of 6..8 vertices on the scale-22 served graph; the
     # selection batch has the served stream's 1:1 mix of insertions and
-    # deletions.  (Dense queries on this graph, with only 8 vertex labels:
-    # none of 432 six-vertex candidates had its sampled updates within the
-    # sample budget and eight heavy updates verifiable.)
-    "served": {"workload": "served", "plan": [("sparse", 6 + i % 3) for i in range(16)],
+    # deletions
+    "served": {"workload": "served", "plan": [("dense", 6 + i % 3) for i in range(16)],
                "stride": 10_000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
                "max_passed": 8, "max_attempts": 6000},
 }

