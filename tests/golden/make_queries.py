@@ -67,13 +67,13 @@ SPECS = {
     "batched": {"workload": "mid", "plan": [("sparse_lt3", 4 + (i // 2) % 3) if i % 2 == 0
                                             else ("dense_ge3", 4 + (i // 2) % 5) for i in range(64)],
                 "stride": 10_000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
-                "max_passed": 8, "max_attempts": 6000},
+                "max_passed": 8, "max_passed_by_size": {7: 24, 8: 24}, "max_attempts": 6000},
     # 16 dense queries of 6..8 vertices on the scale-22 served graph; the
     # selection batch has the served stream's 1:1 mix of insertions and
     # deletions
     "served": {"workload": "served", "plan": [("dense", 6 + i % 3) for i in range(16)],
                "stride": 10_000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
-               "max_passed": 8, "max_attempts": 6000},
+               "max_passed": 8, "max_passed_by_size": {7: 24, 8: 24}, "max_attempts": 6000},
 }
 TOP_PER_PAIR = 64  # heavy candidates kept per endpoint-label pair
 
@@ -154,6 +154,25 @@ def check_pairs(sess, Q, table, prod, sample, spec, strict_sample, max_passed=No
     return got, heavy, passed, None
 
 
+def rule_text(spec):
+    """The selection rule, in words, as stored with the queries."""
+    return ("keep a candidate when the CPU oracle verifies its check set on the selection batch: every %d-th "
+            "update within %d candidate tests each, and the %d heaviest verifiable updates (going down the updates "
+            "whose endpoint labels match one of the query's edges by decreasing endpoint-degree product, the first "
+            "%d finished within %d candidate tests each; heavier ones are passed over and counted%s); the check "
+            "set must hold an incremental match; at most %d attempts per (class, size), no fall to smaller sizes" % (
+                spec["stride"], spec["sample_budget"], spec["heavy"], spec["heavy"], spec["heavy_budget"],
+                (", at most %d of them" % spec["max_passed"] +
+                 "".join(", %d for %d vertices" % (v, k) for k, v in sorted(spec.get("max_passed_by_size", {}).items())))
+                if spec.get("max_passed") else "",
+                spec["max_attempts"]))
+
+
+def max_passed_for(spec, q):
+    """Heavy candidates a q-vertex query may pass over (None: no limit)."""
+    return spec.get("max_passed_by_size", {}).get(q, spec.get("max_passed"))
+
+
 def _init(name):
     global _S
     spec = SPECS[name]
@@ -176,7 +195,7 @@ def _try(args):
         return attempt, None, "class test failed"
     t = time.time()
     got, heavy, passed, why = check_pairs(sess, Q, table, prod, sample, spec, strict_sample=True,
-                                          max_passed=spec.get("max_passed"))
+                                          max_passed=max_passed_for(spec, q))
     if why is not None:
         return attempt, None, why
     if sum(got.values()) == 0:
@@ -204,14 +223,7 @@ def main():
         return merge(args.name)
     _init(args.name)
     w, b = _S[1], _S[2]
-    rule = ("keep a candidate when the CPU oracle verifies its check set on the selection batch: every %d-th "
-            "update within %d candidate tests each, and the %d heaviest verifiable updates (going down the updates "
-            "whose endpoint labels match one of the query's edges by decreasing endpoint-degree product, the first "
-            "%d finished within %d candidate tests each; heavier ones are passed over and counted%s); the check "
-            "set must hold an incremental match; at most %d attempts per (class, size), no fall to smaller sizes" % (
-                spec["stride"], spec["sample_budget"], spec["heavy"], spec["heavy"], spec["heavy_budget"],
-                ", at most %d of them" % spec["max_passed"] if spec.get("max_passed") else "",
-                spec["max_attempts"]))
+    rule = rule_text(spec)
     out = {"workload": spec["workload"], "graph_digest": w.graph.digest(), "selection_batch_updates": len(b),
            "rule": rule, "queries": [], "rejected": {}}
     want = {}
@@ -285,7 +297,8 @@ def merge(name):
     keys = [json.dumps([d["labels"], d["edges"]]) for v in chosen.values() for d in v]
     if len(set(keys)) != len(keys):
         raise SystemExit("the partial files hold the same query twice")
-    out = {k: head[k] for k in ("workload", "graph_digest", "selection_batch_updates", "rule")}
+    out = {k: head[k] for k in ("workload", "graph_digest", "selection_batch_updates")}
+    out["rule"] = rule_text(spec)
     out["queries"], out["rejected"] = [], rejected
     used = {}
     for kind, q in spec["plan"]:
