@@ -44,6 +44,14 @@ import numpy as np  # noqa: E402
 from oracle import oracle as O  # noqa: E402
 from paper_2401_17018_gb300 import inputs as I  # noqa: E402
 
+def interleave(a, b):
+    """a[0], b[0], a[1], b[1], ... and then the rest of the longer list."""
+    out = []
+    for i in range(max(len(a), len(b))):
+        out += a[i:i + 1] + b[i:i + 1]
+    return out
+
+
 SPECS = {
     # 6-vertex queries (the paper's default size), 4 sparse and 4 dense, on
     # the scale-23 graph; selected on the first of the five consecutive
@@ -58,14 +66,18 @@ SPECS = {
     "mid": {"workload": "mid", "plan": [("sparse", 6)] * 10 + [("dense", 6)] * 10,
             "stride": 1000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
             "max_attempts": 4000},
-    # 64 queries, sparse (average degree < 3) of 4..6 vertices and dense
-    # (average degree >= 3, the paper's Dense class) of 4..8 vertices
-    # alternating, on the mid graph.  Larger ones were not verifiable: of 20
-    # dense 9-vertex and 264 sparse 9-vertex candidates and 72 sparse
-    # 7-vertex ones, none had its sampled and eight heavy updates within the
-    # budgets.
-    "batched": {"workload": "mid", "plan": [("sparse_lt3", 4 + (i // 2) % 3) if i % 2 == 0
-                                            else ("dense_ge3", 4 + (i // 2) % 5) for i in range(64)],
+    # 64 queries of 4..7 vertices, on the mid graph: 38 sparse (average
+    # degree < 3) of 4..6 vertices and 26 dense (average degree >= 3, the
+    # paper's Dense class) of 4..7, the two classes alternating while both
+    # last.  Larger ones were not verifiable: of 20 dense 9-vertex, 264
+    # sparse 9-vertex, 72 sparse 7-vertex and 32 dense 8-vertex candidates,
+    # none had its sampled updates within the sample budget and eight heavy
+    # updates verifiable (dense 8-vertex ones that were took 6 to 25 minutes
+    # of oracle time each, without the passed-over cap).
+    "batched": {"workload": "mid", "plan": interleave([("sparse_lt3", q) for q, n in ((4, 14), (5, 14), (6, 10))
+                                                       for _ in range(n)],
+                                                      [("dense_ge3", q) for q, n in ((4, 7), (5, 7), (6, 6), (7, 6))
+                                                       for _ in range(n)]),
                 "stride": 10_000, "sample_budget": 10_000_000, "heavy": 8, "heavy_budget": 100_000_000,
                 "max_passed": 8, "max_passed_by_size": {7: 24, 8: 24}, "max_attempts": 6000},
     # 16 dense queries of 6..8 vertices on the scale-22 served graph; the
@@ -216,6 +228,8 @@ def main():
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--kind", default=None, help="select only this class (the partial results are merged by --merge)")
     ap.add_argument("--sizes", default=None, help="select only these sizes, e.g. 7,8 (with --kind)")
+    ap.add_argument("--need", type=int, default=0,
+                    help="with --kind: keep up to this many per size instead of the plan's count")
     ap.add_argument("--merge", action="store_true", help="merge the per-class partial files into the output")
     args = ap.parse_args()
     spec = SPECS[args.name]
@@ -231,43 +245,65 @@ def main():
     for kind, q in spec["plan"]:
         if (args.kind is None or kind == args.kind) and (args.sizes is None or q in sizes):
             want[(kind, q)] = want.get((kind, q), 0) + 1
+    if args.need and args.kind is not None:
+        want = {c: args.need for c in want}
     chosen = {c: [] for c in want}
     seen = set()
     ctx = get_context("fork")  # the workers share the parent's graph and oracle session
     t0 = time.time()
+    partial = None
+    if args.kind is not None:
+        partial = os.path.join(HERE, "queries_%s.%s%s.partial" % (
+            args.name, args.kind, ".q" + "-".join(str(q) for q in sorted(sizes)) if sizes else ""))
+    rej_log = {}
+
+    def write_partial(complete):
+        # results arrive in attempt order, so the queries kept so far are the
+        # first ones of their group among the attempts examined so far
+        out["chosen"] = {"%s:%d" % k: v for k, v in chosen.items()}
+        out["rejections"] = rej_log
+        out["complete"] = complete
+        with open(partial, "w") as f:
+            json.dump(out, f, indent=1)
+
     with ctx.Pool(args.workers) as pool:
         for (kind, q), need in sorted(want.items()):
             got = chosen[(kind, q)]
             attempt = 0
             rej = out["rejected"].setdefault("%s:%d" % (kind, q), {})
+            log = rej_log.setdefault("%s:%d" % (kind, q), [])
             while len(got) < need and attempt < spec["max_attempts"]:
                 jobs = [(kind, q, a) for a in range(attempt, min(attempt + args.workers * 4, spec["max_attempts"]))]
                 attempt += len(jobs)
                 print("%s %d: attempts %d, kept %d, rejected %s [%.0fs]" % (kind, q, attempt - len(jobs), len(got),
                                                                          json.dumps(rej), time.time() - t0), flush=True)
                 for att, d, why in pool.imap(_try, jobs):
+                    if len(got) >= need:
+                        break
                     if why is not None:
                         rej[why] = rej.get(why, 0) + 1
+                        log.append([att, why])
                         continue
                     key = json.dumps([d["labels"], d["edges"]])
-                    if key in seen or len(got) >= need:
+                    if key in seen:
+                        log.append([att, "the same query as an earlier attempt"])
                         continue
                     seen.add(key)
                     got.append(d)
                     print("keep %s %d attempt %d: sample %d heavy %d (%.1fs) [%.0fs]" % (
                         kind, q, att, d["sample_matches"], d["heavy_matches"], d["check_seconds"],
                         time.time() - t0), flush=True)
+                    if partial:
+                        write_partial(False)
             rej["attempts"] = attempt
             if len(got) < need:
+                if partial:
+                    write_partial(False)
                 raise SystemExit("found only %d of %d %s queries of %d vertices in %d attempts" % (
                     len(got), need, kind, q, attempt))
-    if args.kind is not None:  # one class: a partial file, merged later
-        out["chosen"] = {"%s:%d" % k: v for k, v in chosen.items()}
-        path = os.path.join(HERE, "queries_%s.%s%s.partial" % (
-            args.name, args.kind, ".q" + "-".join(str(q) for q in sorted(sizes)) if sizes else ""))
-        with open(path, "w") as f:
-            json.dump(out, f, indent=1)
-        print("wrote", path, "in %.0f s" % (time.time() - t0))
+    if partial:  # one class: a partial file, merged later
+        write_partial(True)
+        print("wrote", partial, "in %.0f s" % (time.time() - t0))
         return
     used = {}
     for kind, q in spec["plan"]:
@@ -284,22 +320,40 @@ def merge(name):
     """Assemble queries_NAME.json from the partial files (one per class, or
     per class and sizes)."""
     spec = SPECS[name]
-    chosen, rejected, head = {}, {}, None
+    chosen, rejected, logs, head = {}, {}, {}, None
     parts = sorted(f for f in os.listdir(HERE) if f.startswith("queries_%s." % name) and f.endswith(".partial"))
     for fn in parts:
         with open(os.path.join(HERE, fn)) as f:
             d = json.load(f)
         head = head or d
         rejected.update(d["rejected"])
+        logs.update(d.get("rejections", {}))
         for key, v in d["chosen"].items():
             k, q = key.split(":")
             chosen[(k, int(q))] = v
-    keys = [json.dumps([d["labels"], d["edges"]]) for v in chosen.values() for d in v]
+    need = {}
+    for kind, q in spec["plan"]:
+        need[(kind, q)] = need.get((kind, q), 0) + 1
+    for c, n in need.items():
+        if len(chosen.get(c, [])) < n:
+            raise SystemExit("the partial files hold %d %s queries of %d vertices, the plan needs %d" % (
+                len(chosen.get(c, [])), c[0], c[1], n))
+        chosen[c] = chosen[c][:n]
+        key = "%s:%d" % c
+        if key in logs:  # rejections among the attempts before the last query used
+            last = chosen[c][-1]["attempt"]
+            r = {}
+            for att, why in logs[key]:
+                if att < last:
+                    r[why] = r.get(why, 0) + 1
+            r["attempts"] = last + 1
+            rejected[key] = r
+    keys = [json.dumps([d["labels"], d["edges"]]) for c in need for d in chosen[c]]
     if len(set(keys)) != len(keys):
         raise SystemExit("the partial files hold the same query twice")
     out = {k: head[k] for k in ("workload", "graph_digest", "selection_batch_updates")}
     out["rule"] = rule_text(spec)
-    out["queries"], out["rejected"] = [], rejected
+    out["queries"], out["rejected"] = [], {c: rejected[c] for c in sorted("%s:%d" % k for k in need)}
     used = {}
     for kind, q in spec["plan"]:
         i = used.get((kind, q), 0)
