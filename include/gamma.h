@@ -66,6 +66,8 @@ extern "C" {
 #define GAMMA_F_SEED_IN_ORDER 0x80u /* create DFS work in update order (default with one staged request:
                                    grouped by each update's higher-degree endpoint, so that warps running
                                    together search around the same vertex); results are the same */
+#define GAMMA_F_SEED_BY_QUERY 0x100u /* batched form: create the DFS work query by query (still one DFS launch),
+                                   so that warps running together search for the same query */
 
 typedef struct gamma_ctx gamma_ctx;
 

@@ -498,6 +498,7 @@ int enqueue_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_s
   // the sorted batch holds both entries of every update only when one request is staged
   // (a later update of an edge shared by several requests has none)
   a.seed_sorted = (ctx->nreq <= 1 && !(ctx->flags & GAMMA_F_SEED_IN_ORDER)) ? 1 : 0;
+  a.qfilter = -1;
   a.tasks = ctx->d_tasks;
   a.sched = ctx->d_sched;
   a.task_seq = ctx->d_task_seq;
@@ -515,7 +516,16 @@ int enqueue_match(gamma_ctx *ctx, int32_t *rows_dev, uint64_t row_cap, int row_s
     if (ctx->group_nplans[gi] == 0) continue;
     a.pair_off = ctx->d_pair_off + (size_t)gi * (np + 1);
     if (per_query) CK(gm_begin_group(ctx->d_st, s));
-    CK(gm_seed(a, s));
+    if (!per_query && (ctx->flags & GAMMA_F_SEED_BY_QUERY) && nq > 1) {
+      // one seeding pass per query into the same work list, one DFS launch
+      for (int j = 0; j < nq; j++) {
+        a.qfilter = j;
+        CK(gm_seed(a, s));
+      }
+      a.qfilter = -1;
+    } else {
+      CK(gm_seed(a, s));
+    }
     CKC(cudaMemsetAsync(ctx->d_task_seq, 0, sizeof(uint32_t) * ctx->tasks_cap, s));
     if (!per_query) { CKC(cudaEventRecord(ctx->ev[3], s)); seeded = true; }
     CK(gm_dfs(a, ctx->num_sms, s));
@@ -846,6 +856,7 @@ int gm_recount_prepare(gamma_ctx *ctx, MatchArgs *a, int *nslots, int *num_sms, 
   m.cu = ctx->sb.cu; m.cv = ctx->sb.cv; m.op = ctx->sb.cop; m.b = ctx->b;
   m.ulab = ctx->d_elab ? ctx->sb.ulab : nullptr;
   m.seed_sorted = 0;  // the recount reuses the staged batch's work items; it seeds nothing
+  m.qfilter = -1;
   m.plans = ctx->d_plans; m.nplans = ctx->nplans;
   m.pair_off = ctx->d_pair_off; m.pair_plans = ctx->d_pair_plans;
   m.grain = ctx->grain;

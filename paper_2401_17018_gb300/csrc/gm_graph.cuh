@@ -76,6 +76,7 @@ struct MatchArgs {
   int share;                   // siblings share last-position candidates (counts only)
   int seed_sorted;             // seed in the order of the sorted batch, each update at its
                                // higher-degree endpoint (needs both entries of every update)
+  int qfilter;                 // seed only the plans of this query slot (-1: all)
   const uint64_t *bkeys;       // the staged batch, sorted: (vertex << 33 | deletion << 32 | key)
   const uint32_t *bvals;       // its tags
   const uint32_t *gstart;      // [groups] first sorted entry of each touched vertex

@@ -291,6 +291,7 @@ __global__ void k_seed(MatchArgs a) {
       for (uint32_t pi = p0; pi < p1; pi++) {
         const int pidx = a.pair_plans[pi];
         const Plan &P = a.plans[pidx];
+        if (a.qfilter >= 0 && P.qslot != a.qfilter) continue;
         if (a.use_filter && !(nlf_ok(g, v1, P, 0) && nlf_ok(g, v2, P, 1))) continue;
         if (g.elab && a.ulab[k] != P.el[1][0]) continue;  // the update's edge label against the query edge's
         if (P.q == 2) {

@@ -23,6 +23,7 @@ GAMMA_F_PER_UPDATE, GAMMA_F_NO_FILTER, GAMMA_F_PER_QUERY, GAMMA_F_GRAPH, GAMMA_F
     0x1, 0x2, 0x4, 0x8, 0x10, 0x20)
 GAMMA_F_NO_SHARE = 0x40
 GAMMA_F_SEED_IN_ORDER = 0x80
+GAMMA_F_SEED_BY_QUERY = 0x100
 
 _NAMES = {0: "GAMMA_OK", -1: "GAMMA_EINVAL", -2: "GAMMA_ENOMEM", -3: "GAMMA_ESTATE",
           -4: "GAMMA_EOVERFLOW", -5: "GAMMA_ETIMEOUT", -6: "GAMMA_ECUDA"}

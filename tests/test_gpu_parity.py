@@ -255,7 +255,7 @@ def test_options_do_not_change_results(G):
     ref = None
     for flags, tile, grain, wpb in [(0, 64, 64, 8), (2, 32, 1, 4), (4, 128, 7, 16), (6, 256, 1024, 2), (32, 64, 64, 8),
                                     (8, 64, 64, 8), (64, 64, 64, 8), (96, 32, 3, 8), (128, 64, 64, 8),
-                                    (132, 32, 1, 4)]:
+                                    (132, 32, 1, 4), (256, 64, 64, 8), (264, 64, 16, 4), (384, 64, 64, 8)]:
         pos, neg, _, _, _ = gpu_run(G, w.graph, qs, b, flags=flags, rows=False, frontier_tile=tile,
                                     steal_grain=grain, warps_per_block=wpb)
         got = (pos.tolist(), neg.tolist())
@@ -264,15 +264,16 @@ def test_options_do_not_change_results(G):
         assert got == ref
 
 
-@pytest.mark.parametrize("flags", [0, 0x20, 0x40, 0x60, 0x80, 0xC0])
+@pytest.mark.parametrize("flags", [0, 0x20, 0x40, 0x60, 0x80, 0xC0, 0x100])
 def test_shared_last_position_equals_oracle(G, flags):
     """Queries whose last vertex (in the matching order) is not adjacent to the
     one before it: K(2,3) with the second side on one label (the sibling
     correction applies) and on two labels, a star, and a 5-cycle with a chord.
     The children of one partial match then share their last-position
     candidates (counted once per sibling); with GAMMA_F_NO_SHARE (0x40) and
-    GAMMA_F_NO_LEAF (0x20) combinations, and with work created in update
-    order (GAMMA_F_SEED_IN_ORDER, 0x80) instead of grouped by hub, the
+    GAMMA_F_NO_LEAF (0x20) combinations, with work created in update order
+    (GAMMA_F_SEED_IN_ORDER, 0x80) instead of grouped by hub, and query by
+    query (GAMMA_F_SEED_BY_QUERY, 0x100), the
     per-update charges stay the oracle's, on a power-law graph with hubs and
     a mixed batch."""
     w = I.make_workload("large", scale=13, n_edges=90_000)
