@@ -434,7 +434,8 @@ def run_served(args):
     g = w.graph
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     d_graph = (dev(g.labels), dev(g.src), dev(g.dst))
-    ctx = G.Context(stream=torch.cuda.Stream(), work_budget=WORK_BUDGET)
+    # the budget bounds one apply, and a served group of up to 64 requests is one apply
+    ctx = G.Context(stream=torch.cuda.Stream(), work_budget=WORK_BUDGET * 64)
 
     def fresh():
         ctx.load_graph(g.n, *d_graph)

@@ -128,17 +128,20 @@ def test_batched_workload(G):
 def test_served_workload(G):
     """The served workload's first requests on the scale-22 graph: applied one
     after another they match the oracle on every check pair; through the
-    server (continuous batching, the requests share edges) each request gets
-    the same counts."""
+    server (continuous batching: the first two requests, staged together as
+    one group) each request gets the same counts.  The work budget bounds
+    one apply, and a group is one apply, so the server's context gets the
+    budget of every request it may group."""
     batches, totals, _, pairs, heavy = _run_batches(G, "served")
     queries, _ = _stored("served")
     w = I.make_workload("served")
     g = w.graph
-    with G.Context(work_budget=WORK_BUDGET) as ctx:
+    reqs = batches[:2]
+    with G.Context(work_budget=WORK_BUDGET * (len(reqs) + 1)) as ctx:
         ctx.load_graph(g.n, g.labels, g.src, g.dst)
         qids = [ctx.register_query(q.labels, q.src, q.dst) for q in queries]
-        srv = G.Server(ctx, qids, max_requests=8)
-        tickets = [srv.submit(b.op, b.src, b.dst) for b in batches]
+        srv = G.Server(ctx, qids, max_requests=len(reqs))
+        tickets = [srv.submit(b.op, b.src, b.dst) for b in reqs]
         for t, (p, n) in zip(tickets, totals):
             rc, pos, neg, info = srv.wait(t)
             assert rc == G.GAMMA_OK
