@@ -318,14 +318,14 @@ def main():
     print("wrote", path, len(out["queries"]), "queries in %.0f s" % (time.time() - t0))
 
 
-def merge(name):
+def merge(name, here=HERE, spec=None):
     """Assemble queries_NAME.json from the partial files (one per class, or
-    per class and sizes)."""
-    spec = SPECS[name]
+    per class and sizes) in ``here``."""
+    spec = spec or SPECS[name]
     chosen, rejected, logs, head = {}, {}, {}, None
-    parts = sorted(f for f in os.listdir(HERE) if f.startswith("queries_%s." % name) and f.endswith(".partial"))
+    parts = sorted(f for f in os.listdir(here) if f.startswith("queries_%s." % name) and f.endswith(".partial"))
     for fn in parts:
-        with open(os.path.join(HERE, fn)) as f:
+        with open(os.path.join(here, fn)) as f:
             d = json.load(f)
         head = head or d
         rejected.update(d["rejected"])
@@ -361,10 +361,11 @@ def merge(name):
         i = used.get((kind, q), 0)
         out["queries"].append(chosen[(kind, q)][i])
         used[(kind, q)] = i + 1
-    path = os.path.join(HERE, "queries_%s.json" % name)
+    path = os.path.join(here, "queries_%s.json" % name)
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print("wrote", path, len(out["queries"]), "queries")
+    return out
 
 
 if __name__ == "__main__":
