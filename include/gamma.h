@@ -338,8 +338,11 @@ GAMMA_API int gamma_recount_noalloc(gamma_ctx *ctx, int32_t cap, uint64_t *out_p
  * hbm_fraction of the free HBM (admission).  A group that contains an
  * invalid request is served again one request at a time, so only the invalid
  * request fails (GAMMA_EINVAL) and the others get their one-at-a-time
- * results.  While a server runs, its context belongs to the worker thread:
- * call nothing else on it.
+ * results.  A group is one apply, so the context's work_budget bounds the
+ * whole group: give it the budget of every request a group may hold, or 0,
+ * else a group can end with GAMMA_ETIMEOUT (for all its requests) although
+ * each request alone stays within the budget.  While a server runs, its
+ * context belongs to the worker thread: call nothing else on it.
  * ------------------------------------------------------------------------ */
 typedef struct gamma_server gamma_server;
 
